@@ -1,0 +1,335 @@
+"""Seeded synthetic particle inputs shaped like the paper's 3-D test cases.
+
+This module only places particles and fills in configuration numbers.  It holds
+none of the method's arithmetic (no kernel, no equation of state, no Riemann
+solver, no hydrostatic density): both the CUDA library and the CPU oracle take
+its output as plain inputs and compute everything else themselves.
+
+Geometry conventions (shared by every generator):
+  * particles sit on a cubic lattice at (k + 1/2) * dp;
+  * a tank of inner size Lx x Ly x Lz has its inner floor at z = 0 and its
+    inner side faces at x = 0, x = Lx, y = 0, y = Ly; it has no roof;
+  * wall dummy particles fill ``layers`` lattice layers outside the floor and
+    the four side faces, up to the tank height (corners included);
+  * the neighbour-grid domain [lo, hi] is the wall bounding box padded by one
+    grid cell (2h) on every side, plus head room above the tank.
+
+Sizes follow the paper's cases (Sec. 4): the smoothing length is h = 1.3 dx
+with support radius 2h, g = 9.81 m/s^2, and the sound speed is chosen as
+c0 = 10 sqrt(g H) with H the initial depth of the heavy phase.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+G = 9.81
+SEED_JITTER = 20211006
+SEED_PROBES = 1
+
+
+@dataclasses.dataclass
+class Phase:
+    rho0: float = 1000.0
+    eos: str = "tait"              # "tait" | "linear"
+    density: str = "continuity"    # "continuity" | "summation"
+    reinit: str = "free_surface"   # "free_surface" | "internal" | "none"
+    penalty: bool = False
+    mu: float = 0.0                # dynamic viscosity [Pa s]
+    z_top: float = 0.0             # top of this phase's column (hydrostatic init)
+
+
+@dataclasses.dataclass
+class Scene:
+    name: str
+    dp: float
+    h: float
+    c0: float
+    g: Tuple[float, float, float]
+    lo: Tuple[float, float, float]
+    hi: Tuple[float, float, float]
+    phases: List[Phase]
+    fluid_pos: np.ndarray            # (N, 3) float64
+    fluid_vel: np.ndarray            # (N, 3) float64
+    fluid_phase: np.ndarray          # (N,) int32
+    wall_pos: np.ndarray             # (M, 3) float64
+    gamma_tait: float = 7.0
+    gamma_p: float = 1.0
+    cfl: float = 0.25
+    reinit_every: int = 1
+    periodic: Tuple[int, int, int] = (0, 0, 0)
+    steps: int = 1
+    probes: Optional[np.ndarray] = None   # indices into wall_pos
+    rho_init: Optional[np.ndarray] = None  # None: hydrostatic initial density
+
+    @property
+    def n_fluid(self) -> int:
+        return int(self.fluid_pos.shape[0])
+
+    @property
+    def n_wall(self) -> int:
+        return int(self.wall_pos.shape[0])
+
+
+def _count(length: float, dp: float) -> int:
+    """Number of lattice sites of spacing dp that fit a length (half rounds up)."""
+    return int(math.floor(length / dp + 0.5))
+
+
+def lattice(n: Tuple[int, int, int], dp: float,
+            origin: Tuple[float, float, float] = (0.0, 0.0, 0.0)) -> np.ndarray:
+    """Points origin + (k + 1/2) dp for k in [0, n) per axis, x fastest."""
+    nx, ny, nz = n
+    kx = (np.arange(nx, dtype=np.float64) + 0.5) * dp + origin[0]
+    ky = (np.arange(ny, dtype=np.float64) + 0.5) * dp + origin[1]
+    kz = (np.arange(nz, dtype=np.float64) + 0.5) * dp + origin[2]
+    z, y, x = np.meshgrid(kz, ky, kx, indexing="ij")
+    return np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+
+
+def tank_walls(inner: Tuple[int, int], height: int, dp: float,
+               layers: int = 3) -> np.ndarray:
+    """Wall dummy particles of an open-top box tank.
+
+    ``inner`` = (nx, ny) lattice sites across the floor, ``height`` = number
+    of lattice layers the side walls rise above the floor.  Returns the
+    lattice sites of the padded box [-layers, n + layers) x ... x
+    [-layers, height) that are not inside the tank.
+    """
+    nx, ny = inner
+    kx = np.arange(-layers, nx + layers)
+    ky = np.arange(-layers, ny + layers)
+    kz = np.arange(-layers, height)
+    z, y, x = np.meshgrid(kz, ky, kx, indexing="ij")
+    x, y, z = x.ravel(), y.ravel(), z.ravel()
+    inside = (x >= 0) & (x < nx) & (y >= 0) & (y < ny) & (z >= 0)
+    keep = ~inside
+    k = np.stack([x[keep], y[keep], z[keep]], axis=1).astype(np.float64)
+    return (k + 0.5) * dp
+
+
+def _domain(wall: np.ndarray, fluid: np.ndarray, cell: float,
+            head_room: float) -> Tuple[tuple, tuple]:
+    pts = wall if wall.shape[0] else fluid
+    lo = pts.min(axis=0) - cell
+    hi = pts.max(axis=0) + cell
+    hi[2] += head_room
+    return tuple(float(v) for v in lo), tuple(float(v) for v in hi)
+
+
+def still_water_tank(n_fluid: Tuple[int, int, int] = (20, 20, 20),
+                     dp: float = 0.01, wall_height: float = 0.3,
+                     layers: int = 3, eos: str = "tait",
+                     steps: int = 100) -> Scene:
+    """Water block filling the floor of an open box tank, at rest.
+
+    Default: a 20^3 block (8,000 particles, dp = 0.01 m) in a 0.2 x 0.2 m
+    tank whose walls rise to 0.3 m, three wall layers.
+    """
+    nx, ny, nz = n_fluid
+    h = 1.3 * dp
+    H = nz * dp
+    fluid = lattice(n_fluid, dp)
+    wall = tank_walls((nx, ny), _count(wall_height, dp), dp, layers)
+    lo, hi = _domain(wall, fluid, 2 * h, 2 * h)
+    c0 = 10.0 * math.sqrt(G * H)
+    return Scene(
+        name=f"still_water_tank_{nx}x{ny}x{nz}_dp{dp:g}", dp=dp, h=h, c0=c0,
+        g=(0.0, 0.0, -G), lo=lo, hi=hi,
+        phases=[Phase(rho0=1000.0, eos=eos, z_top=H)],
+        fluid_pos=fluid, fluid_vel=np.zeros_like(fluid),
+        fluid_phase=np.zeros(fluid.shape[0], np.int32), wall_pos=wall,
+        reinit_every=1, steps=steps)
+
+
+def dam_break(tank: Tuple[float, float, float] = (1.6, 0.67, 0.6),
+              column: Tuple[float, float, float] = (0.4, 0.67, 0.3),
+              dp: float = 0.01, layers: int = 3, penalty: bool = True,
+              reinit_every: int = 20, steps: int = 2000,
+              mu: float = 0.0, n_probes: int = 0) -> Scene:
+    """Single-phase 3-D dam break: a water column at the x = 0 end of a box.
+
+    Defaults: tank 1.6 x 0.67 x 0.6 m, column 0.4 x 0.67 x 0.3 m, dp = 0.01
+    (80,400 fluid and 120,234 wall particles), penalty on, density
+    reinitialisation every 20 steps.  With ``n_probes`` > 0 a square grid of
+    probe wall particles is chosen on the inner layer of the far wall
+    (x = Lx side) over z in [0, column height].
+    """
+    ntx, nty, ntz = (_count(v, dp) for v in tank)
+    ncx, ncy, ncz = (_count(v, dp) for v in column)
+    h = 1.3 * dp
+    H = ncz * dp
+    fluid = lattice((ncx, ncy, ncz), dp)
+    wall = tank_walls((ntx, nty), ntz, dp, layers)
+    lo, hi = _domain(wall, fluid, 2 * h, 0.25 * tank[2])
+    probes = None
+    if n_probes > 0:
+        side = int(round(math.sqrt(n_probes)))
+        x_in = ntx * dp + 0.5 * dp
+        cand = np.where(np.abs(wall[:, 0] - x_in) < 0.25 * dp)[0]
+        cand = cand[(wall[cand, 2] > 0.0) & (wall[cand, 2] < H)
+                    & (wall[cand, 1] > 0.0) & (wall[cand, 1] < nty * dp)]
+        ky = np.floor(wall[cand, 1] / dp).astype(np.int64)
+        kz = np.floor(wall[cand, 2] / dp).astype(np.int64)
+        ys, zs = np.unique(ky), np.unique(kz)
+        ysel = ys[np.linspace(0, len(ys) - 1, side).round().astype(int)]
+        zsel = zs[np.linspace(0, len(zs) - 1, side).round().astype(int)]
+        pick = np.isin(ky, ysel) & np.isin(kz, zsel)
+        probes = np.sort(cand[pick]).astype(np.int64)
+    return Scene(
+        name=(f"dam_break_{tank[0]:g}x{tank[1]:g}x{tank[2]:g}"
+              f"_col{column[0]:g}x{column[1]:g}x{column[2]:g}_dp{dp:g}"),
+        dp=dp, h=h, c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G),
+        lo=lo, hi=hi,
+        phases=[Phase(rho0=1000.0, eos="tait", penalty=penalty, mu=mu,
+                      z_top=H)],
+        fluid_pos=fluid, fluid_vel=np.zeros_like(fluid),
+        fluid_phase=np.zeros(fluid.shape[0], np.int32), wall_pos=wall,
+        reinit_every=reinit_every, steps=steps, probes=probes)
+
+
+def two_phase_ramp_cylinder(tank: Tuple[float, float, float] = (1.0, 0.5, 0.5),
+                            column: Tuple[float, float, float] = (0.3, 0.5, 0.2),
+                            dp: float = 0.005, layers: int = 3,
+                            ramp_x0: float = 0.5, ramp_deg: float = 30.0,
+                            cyl_xy: Tuple[float, float] = (0.75, 0.25),
+                            cyl_r: float = 0.05, steps: int = 500) -> Scene:
+    """Water column plus air filling the rest of a closed-top box, with an
+    inclined ramp and a vertical cylinder obstacle.
+
+    Water (rho0 = 1000, continuity density) occupies x < column[0],
+    z < column[2]; air (rho0 = 1, summation density, penalty on) fills every
+    other site inside the tank that is outside the obstacles.  The ramp is
+    the half space below the plane through (ramp_x0, z = 0) rising at
+    ``ramp_deg`` towards +x; the cylinder is vertical at ``cyl_xy``.  Obstacle
+    wall particles are the lattice sites with -layers*dp < sdf <= 0.  The box
+    also has a roof (air must be contained).
+    """
+    ntx, nty, ntz = (_count(v, dp) for v in tank)
+    ncx, ncz = _count(column[0], dp), _count(column[2], dp)
+    h = 1.3 * dp
+    H = ncz * dp
+    inner = lattice((ntx, nty, ntz), dp)
+    tan = math.tan(math.radians(ramp_deg))
+    cosr = math.cos(math.radians(ramp_deg))
+
+    def sdf_obstacles(p: np.ndarray) -> np.ndarray:
+        # signed distance, negative inside solid
+        ramp = (p[:, 2] - tan * (p[:, 0] - ramp_x0)) * cosr
+        cyl = np.hypot(p[:, 0] - cyl_xy[0], p[:, 1] - cyl_xy[1]) - cyl_r
+        return np.minimum(ramp, cyl)
+
+    s = sdf_obstacles(inner)
+    fluid_mask = s > 0.0
+    obstacle_wall = inner[(s <= 0.0) & (s > -layers * dp)]
+    fluid = inner[fluid_mask]
+    water = (fluid[:, 0] < ncx * dp) & (fluid[:, 2] < H)
+    phase = np.where(water, 0, 1).astype(np.int32)
+    # closed box: walls on all six faces
+    kx = np.arange(-layers, ntx + layers)
+    ky = np.arange(-layers, nty + layers)
+    kz = np.arange(-layers, ntz + layers)
+    z, y, x = np.meshgrid(kz, ky, kx, indexing="ij")
+    x, y, z = x.ravel(), y.ravel(), z.ravel()
+    inside = ((x >= 0) & (x < ntx) & (y >= 0) & (y < nty)
+              & (z >= 0) & (z < ntz))
+    box = (np.stack([x[~inside], y[~inside], z[~inside]], axis=1)
+           .astype(np.float64) + 0.5) * dp
+    wall = np.concatenate([box, obstacle_wall], axis=0)
+    lo, hi = _domain(wall, fluid, 2 * h, 0.0)
+    c0 = 10.0 * math.sqrt(G * H)
+    return Scene(
+        name=(f"two_phase_ramp_cylinder_{tank[0]:g}x{tank[1]:g}x{tank[2]:g}"
+              f"_dp{dp:g}"),
+        dp=dp, h=h, c0=c0, g=(0.0, 0.0, -G), lo=lo, hi=hi,
+        phases=[Phase(rho0=1000.0, eos="linear", density="continuity",
+                      reinit="free_surface", penalty=False, z_top=H),
+                Phase(rho0=1.0, eos="linear", density="summation",
+                      reinit="internal", penalty=True, z_top=ntz * dp)],
+        fluid_pos=fluid, fluid_vel=np.zeros_like(fluid), fluid_phase=phase,
+        wall_pos=wall, reinit_every=1, steps=steps)
+
+
+def two_phase_still_tank(n: Tuple[int, int] = (12, 6), dp: float = 0.01,
+                         water_layers: int = 6, air_layers: int = 6,
+                         layers: int = 3) -> Scene:
+    """Closed box with water below and air above, both at rest (a 3-D,
+    thin-box stand-in for the paper's two-phase hydrostatic tank)."""
+    nx, ny = n
+    nz = water_layers + air_layers
+    h = 1.3 * dp
+    H = water_layers * dp
+    fluid = lattice((nx, ny, nz), dp)
+    phase = np.where(fluid[:, 2] < H, 0, 1).astype(np.int32)
+    kx = np.arange(-layers, nx + layers)
+    ky = np.arange(-layers, ny + layers)
+    kz = np.arange(-layers, nz + layers)
+    z, y, x = np.meshgrid(kz, ky, kx, indexing="ij")
+    x, y, z = x.ravel(), y.ravel(), z.ravel()
+    inside = ((x >= 0) & (x < nx) & (y >= 0) & (y < ny) & (z >= 0) & (z < nz))
+    wall = (np.stack([x[~inside], y[~inside], z[~inside]], axis=1)
+            .astype(np.float64) + 0.5) * dp
+    lo, hi = _domain(wall, fluid, 2 * h, 0.0)
+    return Scene(
+        name=f"two_phase_still_tank_{nx}x{ny}x{nz}_dp{dp:g}", dp=dp, h=h,
+        c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G), lo=lo, hi=hi,
+        phases=[Phase(rho0=1000.0, eos="linear", density="continuity",
+                      reinit="free_surface", penalty=False, z_top=H),
+                Phase(rho0=1.0, eos="linear", density="summation",
+                      reinit="internal", penalty=True, z_top=nz * dp)],
+        fluid_pos=fluid, fluid_vel=np.zeros_like(fluid), fluid_phase=phase,
+        wall_pos=wall, reinit_every=1, steps=100)
+
+
+def jittered_blob(n: Tuple[int, int, int] = (16, 16, 16), dp: float = 0.01,
+                  jitter: float = 0.05, vel_scale: float = 0.1,
+                  rho_jitter: float = 0.0, seed: int = SEED_JITTER,
+                  margin_cells: int = 4, eos: str = "tait") -> Scene:
+    """Free fluid blob, no walls, no gravity: lattice sites moved by a
+    uniform random jitter of +-jitter*dp, with random velocities of scale
+    ``vel_scale`` (m/s).  Used for conservation checks."""
+    rng = np.random.default_rng(seed)
+    h = 1.3 * dp
+    pos = lattice(n, dp)
+    pos = pos + rng.uniform(-jitter, jitter, size=pos.shape) * dp
+    vel = rng.normal(0.0, vel_scale, size=pos.shape)
+    lo = tuple(float(v) for v in (pos.min(axis=0) - margin_cells * 2 * h))
+    hi = tuple(float(v) for v in (pos.max(axis=0) + margin_cells * 2 * h))
+    sc = Scene(
+        name=f"jittered_blob_{n[0]}x{n[1]}x{n[2]}_dp{dp:g}", dp=dp, h=h,
+        c0=10.0, g=(0.0, 0.0, 0.0), lo=lo, hi=hi,
+        phases=[Phase(rho0=1000.0, eos=eos, reinit="none",
+                      z_top=float(pos[:, 2].max()))],
+        fluid_pos=pos, fluid_vel=vel,
+        fluid_phase=np.zeros(pos.shape[0], np.int32),
+        wall_pos=np.zeros((0, 3)), reinit_every=0)
+    if rho_jitter > 0.0:
+        sc.rho_init = 1000.0 * (1.0 + rng.uniform(-rho_jitter, rho_jitter,
+                                                  size=pos.shape[0]))
+    return sc
+
+
+def random_points(n: int, box: Tuple[float, float, float], seed: int,
+                  dp: float = 0.01) -> np.ndarray:
+    """n uniform random points in [0, box) (for neighbour-search checks)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(0.0, 1.0, size=(n, 3)) * np.asarray(box)
+
+
+def standard(name: str) -> Scene:
+    """The workloads the benchmark and the parity tests are defined on."""
+    if name == "still_water_8k":
+        return still_water_tank()
+    if name == "dam_break_80k":
+        return dam_break()
+    if name == "two_phase_ramp_cylinder":
+        return two_phase_ramp_cylinder()
+    if name == "dam_break_adjoint_189k":
+        return dam_break(dp=0.0075, steps=10, n_probes=64)
+    if name == "dam_break_10m":
+        return dam_break(tank=(3.2, 1.0, 1.0), column=(1.2, 1.0, 0.55),
+                         dp=0.004, steps=200)
+    raise KeyError(name)
