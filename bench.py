@@ -1,0 +1,415 @@
+"""Benchmark of the WCSPH wall-boundary step (arXiv 2110.02621) on GB300.
+
+Workload: the 3-D single-phase dam break (tank 1.6 x 0.67 x 0.6 m, water
+column 0.4 x 0.67 x 0.3 m, dp = 0.01 m: 80,400 fluid and 120,234 wall
+particles, Tait EOS, penalty on, density reinitialisation every 20 steps),
+FP32, synthetic lattice input.  One benchmark step = one sph_step time step
+(re-bin and sort, continuity, wall pressure, momentum, integration), timed
+with CUDA events on the library's stream, with a 256 MB write between steps
+so that every step starts with a cold L2.
+
+Metric: M particle-steps/s, particles = fluid + wall particles with fluid
+support in that step.  One JSON line on stdout (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank runs an independent replica (the step has no
+data-parallel split without a halo exchange, so replicas only); value sums the
+ranks' particle-steps over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "M particle-steps/s FP32 vs FP64 GPU at stated error; adjoint/forward time"
+UNIT = "M particle-steps/s"
+WORKLOAD = "dam_break_80k"
+
+# Algorithmic floating-point operations per in-support pair (add, sub, mul,
+# div, sqrt = 1; fma = 2), counted from the pair formulas as the kernels
+# evaluate them (kernel table).
+FLOPS_PAIR = {
+    "momentum_ff": 50,      # Riemann p*, limiter, pressure force, sigma
+    "momentum_fw": 40,      # Eq. (RSatWall) pressure force, sigma (penalty rarely active)
+    "continuity_ff": 36,    # Riemann continuity term
+    "continuity_fw": 33,
+    "wall_pressure": 24,    # extrapolation sums
+}
+FP32_LANES_PER_SM = 128
+N_SM = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def scene():
+    from paper_2110_02621_gb300 import scenes
+    return scenes.dam_break()
+
+
+def pair_counts(x_f: np.ndarray, x_w: np.ndarray, h: float):
+    """Exact numbers of (ordered) fluid-fluid, fluid-wall pairs within 2h and
+    of wall particles with fluid support (cKDTree, host)."""
+    from scipy.spatial import cKDTree
+    tf = cKDTree(x_f)
+    ff = tf.count_neighbors(tf, 2 * h * (1 - 1e-12)) - len(x_f)
+    if len(x_w):
+        tw = cKDTree(x_w)
+        fw = tf.count_neighbors(tw, 2 * h * (1 - 1e-12))
+        near = tw.query_ball_tree(tf, 2 * h * (1 - 1e-12))
+        active = sum(1 for v in near if v)
+    else:
+        fw, active = 0, 0
+    return int(ff), int(fw), int(active)
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2110_02621_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    entry = rec.get(kernel)
+    if not entry or entry.get("source_hash") != kernel_source_hash():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+# --------------------------------------------------------------- CPU oracle
+def cpu_baseline(sc, active_walls: float, seconds: float):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the same workload (whole steps of the full dam break)."""
+    import oracle
+    oracle.build()
+    sim = oracle.OracleSim(sc)
+    t0 = time.perf_counter()
+    sim.step(1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(50, int(seconds / max(t1, 1e-3)) - 1))
+    t0 = time.perf_counter()
+    sim.step(n)
+    el = time.perf_counter() - t0
+    steps = n + 1
+    total = el + t1
+    parts = sc.n_fluid + active_walls
+    sim.close()
+    return {"value": parts * steps / total / 1e6, "unit": UNIT, "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"{steps} full steps of the {sc.n_fluid}-fluid/{sc.n_wall}-wall dam break "
+                      f"({total:.1f} s, FP64 C oracle, OpenMP over particles)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    sc = scene()
+    import oracle
+    oracle.build()
+    sim = oracle.OracleSim(sc)
+    for _ in range(min(args.warmup, 1)):
+        sim.step(1)
+    t0 = time.perf_counter()
+    sim.step(1)
+    t1 = time.perf_counter() - t0
+    budget = 60.0
+    n = max(1, min(args.steps, int(budget / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    sim.step(n)
+    el = time.perf_counter() - t0
+    _, _, active = pair_counts(sim.fluid()["x"], sc.wall_pos, sc.h)
+    parts = sc.n_fluid + active
+    value = parts * n / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": n, "warmup": args.warmup, "ms_per_step": el / n * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n_fluid": sc.n_fluid,
+                                            "n_wall": sc.n_wall, "dp": sc.dp},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(),
+                             "kind": "oracle",
+                             "sample": f"{n} of the requested {args.steps} steps (bounded to "
+                                       f"about {budget:.0f} s) of the full workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    from paper_2110_02621_gb300 import build, sph
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    if rank == 0:
+        build.build()
+    if pg:
+        pg.barrier()
+    build.build()
+    sph.lib()
+    precision = sph.SPH_FP64_PLAIN if args.precision == "fp64" else sph.SPH_FP32
+    sc = scene()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    sim = sph.Simulation(sc, precision=precision, stream=stream.cuda_stream)
+    # warm-up steps, all kernel kinds timed to find the dominant one
+    sim.profile(sph.KERNEL_KINDS)
+    for _ in range(args.warmup):
+        flush.zero_()
+        sim.step(1)
+    warm = sim.profile_read()
+    step_kinds = [k for k in sph.KERNEL_KINDS if k != "other"]
+    dominant = max(step_kinds, key=lambda k: warm[k]["ms"])
+    warm_total = sum(warm[k]["ms"] for k in step_kinds)
+    shares = {k: round(warm[k]["ms"] / warm_total, 4) for k in step_kinds if warm_total > 0}
+
+    st0 = sim.state()
+    ff, fw, active0 = pair_counts(st0["x"], sc.wall_pos, sc.h)
+    steps0, act_steps0 = sim.counters()
+    launches0 = sum(v["launches"] for v in sim.profile_read().values())
+
+    sim.profile([dominant])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.perf_counter()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_ms = float(sum(step_ms))
+    prof = sim.profile_read()
+    steps1, act_steps1 = sim.counters()
+    launches1 = sum(v["launches"] for v in prof.values())
+    active_mean = (act_steps1 - act_steps0) / max(steps1 - steps0, 1)
+    dom_ms = prof[dominant]["ms"] / max(prof[dominant]["timed"], 1)
+    st1 = sim.state()
+    ff1, fw1, active1 = pair_counts(st1["x"], sc.wall_pos, sc.h)
+    sim.close()
+
+    if pg:
+        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_ms = float(t.item())
+    parts = sc.n_fluid + active_mean
+    value = world * parts * args.steps / (t_ms / 1e3) / 1e6
+    value_fluid = world * sc.n_fluid * args.steps / (t_ms / 1e3) / 1e6
+
+    # roofline of the dominant kernel (FP32 ALU bound: no dense contraction)
+    pairs_ff = 0.5 * (ff + ff1)
+    pairs_fw = 0.5 * (fw + fw1)
+    if dominant == "momentum":
+        flops = pairs_ff * FLOPS_PAIR["momentum_ff"] + pairs_fw * FLOPS_PAIR["momentum_fw"]
+    elif dominant == "continuity":
+        flops = pairs_ff * FLOPS_PAIR["continuity_ff"] + pairs_fw * FLOPS_PAIR["continuity_fw"]
+    elif dominant == "wall_pressure":
+        flops = pairs_fw * FLOPS_PAIR["wall_pressure"]
+    else:
+        flops = None
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    roofline = None
+    if flops:
+        ach = flops / (dom_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": f"k_{dominant}", "achieved": ach, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                    "traffic": ncu_traffic(f"k_{dominant}"),
+                    "peak_source": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
+                                   f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
+                    "flops_per_launch": flops, "ms_per_launch": dom_ms}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if precision == sph.SPH_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_fluid": sc.n_fluid, "n_wall": sc.n_wall,
+                       "active_wall_mean": round(active_mean, 1), "dp": sc.dp,
+                       "value_fluid_only": value_fluid, "l2": "256 MB write before every timed step",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "kernel_share_warmup": shares},
+            "roofline": roofline, "gpu_launches": int(launches1 - launches0), "clocks": clk,
+            "host_wall_s": wall1 - wall0}
+
+    if rank == 0 and world == 1 and not args.no_e2e:
+        line["e2e"] = e2e(sc, args.steps, precision, stream, active_mean)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc, active_mean, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
+    return 0
+
+
+def e2e(sc, steps, precision, stream, active_mean):
+    """The same metric through the public C ABI with host buffers: create from
+    pinned host arrays (H2D inside), then per step sph_step plus a device-to-
+    host read of the FP64 diagnostics, then the final state back to the host."""
+    import torch
+    from paper_2110_02621_gb300 import sph
+
+    def pinned(a, dtype):
+        t = torch.empty(a.shape, dtype=dtype, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+
+    x = pinned(sc.fluid_pos, torch.float64)
+    v = pinned(sc.fluid_vel, torch.float64)
+    ph = pinned(sc.fluid_phase, torch.int32)
+    xw = pinned(sc.wall_pos, torch.float64)
+    nf, nw = sc.n_fluid, sc.n_wall
+    outs = {k: torch.empty(shape, dtype=torch.float64, pin_memory=True)
+            for k, shape in (("x", (nf, 3)), ("v", (nf, 3)), ("rho", (nf,)), ("p", (nf,)),
+                             ("pw", (nw,)))}
+    diag = torch.empty(8, dtype=torch.float64, pin_memory=True)
+    params = sph.make_params(sc, precision)
+    fluid = sph.sph_fluid(nf, x.data_ptr(), v.data_ptr(), None, ph.data_ptr())
+    wall = sph.sph_wall(nw, xw.data_ptr())
+    out = sph.sph_state_out(outs["x"].data_ptr(), outs["v"].data_ptr(), outs["rho"].data_ptr(),
+                            outs["p"].data_ptr(), None, None, None, outs["pw"].data_ptr(), None, None)
+    L = sph.lib()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, ctx = sph.sph_create(params, fluid, wall, stream.cuda_stream)
+    assert st == sph.SPH_OK, sph.sph_last_error(None)
+    for _ in range(steps):
+        assert L.sph_step(ctx, 1, 0.0, None) == sph.SPH_OK
+        assert L.sph_diagnostics(ctx, diag.data_ptr()) == sph.SPH_OK
+    assert sph.sph_get_state(ctx, out, sph.SPH_HOST) == sph.SPH_OK
+    el = time.perf_counter() - t0
+    sph.sph_destroy(ctx)
+    h2d = nf * (3 + 3) * 8 + nf * 4 + nw * 3 * 8
+    d2h = 8 * 8 * steps + sum(t.numel() * 8 for t in outs.values())
+    return {"value": (nf + active_mean) * steps / el / 1e6, "unit": UNIT,
+            "h2d_bytes_per_step": h2d / steps, "d2h_bytes_per_step": d2h / steps,
+            "seconds": el, "includes": "sph_create (upload, sort, normals) + steps x (sph_step + "
+                                       "sph_diagnostics D2H) + sph_get_state(HOST)"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,243 @@
+/*
+ * sph.h -- C ABI of the GB300 (sm_103a) implementation of one weakly-
+ * compressible SPH time step with the generalised wall boundary treatment of
+ * Rezavand, Zhang & Hu, "Generalised and efficient wall boundary condition
+ * treatment in GPU-accelerated smoothed particle hydrodynamics" (arXiv
+ * 2110.02621).
+ *
+ * The problem statement follows Sec. 2 and Sec. 3 of the paper: a set of
+ * fluid particles (one or two phases) and a fixed set of wall dummy
+ * particles, a smoothing length h with support radius 2h, an equation of
+ * state per phase, and a one-time upload of the particle data after which
+ * every step runs on the device ("copy the simulation data once at the
+ * beginning ... and vice versa when we need to save the computational
+ * results", Sec. 3).
+ *
+ * Conventions for every call:
+ *   - Every call returns sph_status; nothing is thrown across the ABI.
+ *   - Host arrays passed in are copied before the call returns; the caller
+ *     keeps ownership.  The library owns all device memory it allocates.
+ *   - Positions and velocities are arrays of n*3 doubles (x, y, z of
+ *     particle 0, then particle 1, ...), in absolute coordinates.
+ *   - Particle identities are the indices of the input arrays ("original
+ *     order"); every output is returned in that order unless stated.
+ *   - All work is enqueued on the CUDA stream given to sph_create (NULL =
+ *     legacy default stream).
+ *   - SPH_ERR_CUDA and SPH_ERR_NONFINITE are sticky: afterwards every call
+ *     on the context returns SPH_ERR_STATE, except sph_last_error and
+ *     sph_destroy.
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_ARG = 1,       /* invalid argument: NULL, size, parameter range  */
+    SPH_ERR_CUDA = 2,      /* a CUDA runtime call failed (sticky)            */
+    SPH_ERR_OOM = 3,       /* device allocation failed                       */
+    SPH_ERR_DOMAIN = 4,    /* fluid particles are outside the grid [lo, hi)  */
+    SPH_ERR_NONFINITE = 5, /* a non-finite acceleration appeared (sticky)    */
+    SPH_ERR_STATE = 6,     /* context unusable after a sticky error          */
+    SPH_ERR_UNSUPPORTED = 7
+} sph_status;
+
+enum { SPH_EOS_LINEAR = 0, SPH_EOS_TAIT = 1 };
+enum { SPH_DENSITY_CONTINUITY = 0, SPH_DENSITY_SUMMATION = 1 };
+enum { SPH_REINIT_NONE = 0, SPH_REINIT_FREE_SURFACE = 1, SPH_REINIT_INTERNAL = 2 };
+enum { SPH_FP32 = 0, SPH_FP64_PLAIN = 1 };
+enum { SPH_HOST = 0, SPH_DEVICE = 1 };
+
+/* One fluid phase (Sec. 2.1: heavy and light phases of a multi-phase flow). */
+typedef struct {
+    double rho0;     /* reference density rho^0 [kg/m^3], > 0                */
+    double mu;       /* dynamic viscosity [Pa s], >= 0 (0: inviscid, as in    *
+                      * the paper); laminar form of Morris et al. (1997)     */
+    double z_top;    /* top of the phase's column; used only for the          *
+                      * hydrostatic start (sph_fluid.rho == NULL)            */
+    int32_t eos;     /* SPH_EOS_LINEAR: Eq. (EoS) p = c^2 (rho - rho0);       *
+                      * SPH_EOS_TAIT:   p = rho0 c^2/gamma ((rho/rho0)^gamma - 1) */
+    int32_t density; /* SPH_DENSITY_CONTINUITY: Eq. (SPH_star_massConservation)
+                      * SPH_DENSITY_SUMMATION:  Eq. (densitySummation)       */
+    int32_t reinit;  /* SPH_REINIT_FREE_SURFACE: Eq. (eqrhosum);              *
+                      * SPH_REINIT_INTERNAL: Eq. (eqrhosumnosurface)         */
+    int32_t penalty; /* 1: penalty force F_p, Eq. (SPH_penaltyMethodTerm),   *
+                      * on this phase's wall interactions                    */
+} sph_phase;
+
+typedef struct {
+    double dp;          /* initial particle spacing dx [m], > 0              */
+    double h;           /* smoothing length [m]; support radius 2h; grid cells*
+                         * are cubes of side 2h                               */
+    double c0;          /* artificial speed of sound, one value for all       *
+                         * phases (Sec. 2.6), > 0                             */
+    double gamma_tait;  /* Tait exponent (7)                                  */
+    double gamma_p;     /* penalty strength gamma_p (1 in the paper)          */
+    double cfl;         /* time-step coefficient (0.25, Sec. 2.6)             */
+    double g[3];        /* body force [m/s^2]                                 */
+    double lo[3];       /* grid origin; particles must stay in [lo, hi)       */
+    double hi[3];
+    int32_t n_phases;   /* 1 or 2                                             */
+    int32_t reinit_every; /* density reinitialisation at the start of steps   *
+                         * n with n % reinit_every == 0 (the paper: every     *
+                         * step, i.e. 1); 0 = only on sph_reinit_density      */
+    sph_phase phase[2];
+    int32_t precision;  /* SPH_FP32: FP32 pair arithmetic, positions as cell  *
+                         * index + FP32 offset with Kahan-compensated drift;  *
+                         * SPH_FP64_PLAIN: the same kernels in FP64           */
+    int32_t reserved;   /* must be 0                                          */
+} sph_params;
+
+/* Fluid particles.  rho may be NULL: each particle then starts from the
+ * hydrostatic pressure of the stacked phase columns (phase k spans
+ * (z_top[k-1], z_top[k]], gravity along -z) converted by the inverse EOS.
+ * phase may be NULL (all phase 0). */
+typedef struct {
+    int64_t n;
+    const double* pos;    /* [n*3] */
+    const double* vel;    /* [n*3], may be NULL (at rest) */
+    const double* rho;    /* [n] or NULL */
+    const int32_t* phase; /* [n] or NULL */
+} sph_fluid;
+
+/* Wall dummy particles: fixed for the whole run (Sec. 2.3). */
+typedef struct {
+    int64_t n;
+    const double* pos;    /* [n*3] */
+} sph_wall;
+
+/* Output buffers of sph_get_state.  Any pointer may be NULL (skipped).  With
+ * where = SPH_HOST they are host memory, with SPH_DEVICE device memory on the
+ * context's device.  Fluid arrays are in original order. */
+typedef struct {
+    double* pos;      /* [n_fluid*3] absolute position                         */
+    double* vel;      /* [n_fluid*3]                                           */
+    double* rho;      /* [n_fluid] density                                     */
+    double* p;        /* [n_fluid] pressure                                    */
+    double* acc;      /* [n_fluid*3] dv/dt at the current state                */
+    double* drho_dt;  /* [n_fluid] d rho/dt of the last continuity update      */
+    double* sigma;    /* [n_fluid] number density sum_j W_ij (self included)   */
+    double* pw;       /* [n_wall] wall dummy pressure p_w, Eq. (wallPressure)  */
+    double* rhow;     /* [n_wall*2] wall density per fluid phase (EOS^-1 p_w)  */
+    double* normal;   /* [n_wall*3] wall normal n_w, Eq. (normalVectors)       */
+} sph_state_out;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Create a simulation (Sec. 3: one upload, then device-resident state).
+ * Validates the arguments, bins and sorts walls (once) and fluid into the
+ * cell grid, computes wall normals (Eq. normalVectors), the initial density
+ * and pressure, the wall pressure (Eq. wallPressure) and the initial
+ * acceleration (Eq. SPH_star_momentumConservation).  cuda_stream is a
+ * cudaStream_t (or NULL).  On success *out owns all device memory until
+ * sph_destroy.  Errors: SPH_ERR_ARG, SPH_ERR_OOM, SPH_ERR_CUDA,
+ * SPH_ERR_DOMAIN (a particle outside [lo, hi)). */
+sph_status sph_create(const sph_params* params, const sph_fluid* fluid,
+                      const sph_wall* wall, void* cuda_stream, sph_ctx** out);
+
+/* Advance nsteps kick-drift-kick steps (Sec. 2.6): reinitialise density if
+ * due (Eqs. eqrhosum / eqrhosumnosurface), half kick and drift, re-bin and
+ * sort, continuity or summation density and EOS, wall pressure, momentum
+ * with penalty, viscosity and gravity, final kick.  dt > 0 fixes the step;
+ * dt <= 0 takes dt = cfl min(h/(c0 + U_max), sqrt(h/|g|)) on the device.
+ * dt_out (may be NULL) receives the last step's dt.  Synchronises the
+ * stream once at the end to read the error word.  Errors: SPH_ERR_ARG
+ * (nsteps < 0), SPH_ERR_DOMAIN (particles left the grid; they are excluded
+ * from all interactions and the count is in sph_last_error),
+ * SPH_ERR_NONFINITE, SPH_ERR_CUDA, SPH_ERR_STATE. */
+sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double dt, double* dt_out);
+
+/* Reinitialise the fluid density now with the number density of the current
+ * positions (Eqs. eqrhosum / eqrhosumnosurface per phase mode), and update
+ * the pressure.  Errors: SPH_ERR_CUDA, SPH_ERR_STATE. */
+sph_status sph_reinit_density(sph_ctx* ctx);
+
+/* Copy the current state into caller buffers (Sec. 3, "save the
+ * computational results"), converted to FP64 and original order.  where =
+ * SPH_HOST or SPH_DEVICE says where the buffers live; the call synchronises
+ * the stream before returning.  Errors: SPH_ERR_ARG, SPH_ERR_CUDA,
+ * SPH_ERR_STATE. */
+sph_status sph_get_state(sph_ctx* ctx, const sph_state_out* out, int32_t where);
+
+/* Neighbour grid of the context: dims[3] cells per axis, n_cells, cell side
+ * (2h).  Any pointer may be NULL. */
+sph_status sph_grid_info(const sph_ctx* ctx, int32_t dims[3], int64_t* n_cells,
+                         double* cell_size);
+
+/* The cell-linked list (Sec. 3, neighbour search) as host arrays:
+ *   key_fluid[id]  cell key (cz*ny + cy)*nx + cx of fluid particle id,
+ *                  0xFFFFFFFF outside the grid;
+ *   order_fluid[k] id of the particle in sorted slot k (sorted by key, id);
+ *   start_fluid[c] first sorted slot of cell c, c in [0, n_cells];
+ *                  start_fluid[n_cells] = number of in-grid particles;
+ * and the same for the walls.  Any pointer may be NULL.  Synchronises. */
+sph_status sph_get_cells(sph_ctx* ctx, uint32_t* key_fluid, int32_t* order_fluid,
+                         int32_t* start_fluid, uint32_t* key_wall,
+                         int32_t* order_wall, int32_t* start_wall);
+
+/* FP64 device reductions of the fluid state: out[8] = {total mass,
+ * momentum x, y, z, kinetic energy, potential energy -sum m g.r, U_max,
+ * number of particles outside the grid}.  Synchronises. */
+sph_status sph_diagnostics(sph_ctx* ctx, double out[8]);
+
+/* Counters since creation: steps taken and the summed number of wall
+ * particles that had fluid support in each step's wall-pressure sweep.
+ * Either pointer may be NULL.  Synchronises. */
+sph_status sph_counters(sph_ctx* ctx, int64_t* steps, int64_t* active_wall_steps);
+
+/* Kernel classes of one step, in launch order (cf. the paper's Table 1:
+ * mass conservation, momentum conservation, BC pressure, density update,
+ * neighbour search including sorting, time integration). */
+enum {
+    SPH_K_BEGIN_STEP = 0,   /* time step from U_max, clear cell counters      */
+    SPH_K_PREDICT = 1,      /* half kick, drift, new cell, cell counts        */
+    SPH_K_SCAN = 2,         /* exclusive scan of cell counts (3 launches)     */
+    SPH_K_SCATTER = 3,      /* first placement by arrival rank                */
+    SPH_K_GATHER = 4,       /* (key, id) order, reinitialisation, EOS         */
+    SPH_K_CONTINUITY = 5,   /* Riemann continuity / summation density, EOS    */
+    SPH_K_WALL_PRESSURE = 6,/* wall dummy pressure, Eq. (wallPressure)        */
+    SPH_K_MOMENTUM = 7,     /* momentum, penalty, viscosity, gravity, kick    */
+    SPH_K_OTHER = 8,        /* create, export, diagnostics                    */
+    SPH_NK = 9
+};
+
+/* Per-kernel timing with CUDA events recorded on the context's stream around
+ * every launch of the kinds whose bit is set in kind_mask (0 = off).  Resets
+ * the accumulated times.  Launch counts are always kept.  Errors:
+ * SPH_ERR_CUDA, SPH_ERR_STATE. */
+sph_status sph_profile(sph_ctx* ctx, uint32_t kind_mask);
+
+/* Read the profile (synchronises): ms[k] = summed event time of the timed
+ * launches of kind k since the last sph_profile call, timed[k] = their
+ * number, launches[k] = all launches of kind k since creation.  Each pointer
+ * may be NULL; arrays have SPH_NK entries. */
+sph_status sph_profile_read(sph_ctx* ctx, double* ms, int64_t* timed, int64_t* launches);
+
+/* Message of the last error on ctx (or of the last failed sph_create when
+ * ctx is NULL).  The string lives until the next call on the context. */
+const char* sph_last_error(const sph_ctx* ctx);
+
+/* Free all device memory of the context.  NULL is ignored. */
+void sph_destroy(sph_ctx* ctx);
+
+/* Stand-alone neighbour binning (Sec. 3, neighbour search including
+ * sorting): for n positions (device array [n*3], FP64) compute each
+ * particle's cell key on the grid of cells of side 2h starting at lo with
+ * dims[3] cells, the particle order sorted by (key, id) and the first
+ * sorted slot of each cell.  Outputs are device arrays: key[n] (per id),
+ * order[n], start[n_cells + 1] with n_cells = dims[0]*dims[1]*dims[2].
+ * Scratch memory is allocated and freed on the stream inside the call.
+ * Errors: SPH_ERR_ARG, SPH_ERR_OOM, SPH_ERR_CUDA. */
+sph_status sph_bin_sort(const double* pos, int64_t n, const double lo[3],
+                        double h, const int32_t dims[3], uint32_t* key,
+                        int32_t* order, int32_t* start, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_GB300_H */

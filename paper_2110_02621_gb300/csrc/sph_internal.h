@@ -1,0 +1,51 @@
+// Internal interface between the C ABI (sph_api.cu) and the two compiled
+// forms of the simulation (FP32 in sim_f32.cu, plain FP64 in sim_f64.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "sph.h"
+
+namespace sph {
+
+int32_t scan_blocks(int64_t n);
+int64_t scan_max_len();
+// out[0..n] = exclusive prefix sums of in[0..n-1] (out[n] = total);
+// sums needs scan_blocks(n) entries.
+void scan_exclusive(const int32_t* in, int32_t n, int32_t* out, int32_t* sums, cudaStream_t st);
+
+struct BinSortScratch {
+    size_t cell, id, rank, tmp_src, tmp_id, counts, start, sums, bytes;
+};
+BinSortScratch bin_sort_scratch_layout(int64_t n, int64_t n_cells);
+cudaError_t bin_sort_run(const double* pos, int32_t n, const double lo[3], double cs,
+                         const int32_t dims[3], uint32_t* key, int32_t* order, int32_t* start,
+                         char* scratch, cudaStream_t st);
+
+struct SimBase {
+    virtual ~SimBase() {}
+    virtual sph_status create(const sph_params& P, const sph_fluid& F, const sph_wall& W) = 0;
+    virtual sph_status step(int32_t nsteps, double dt, double* dt_out) = 0;
+    virtual sph_status reinit() = 0;
+    virtual sph_status get_state(const sph_state_out& o, int32_t where) = 0;
+    virtual sph_status get_cells(uint32_t* kf, int32_t* of, int32_t* sf, uint32_t* kw, int32_t* ow,
+                                 int32_t* sw) = 0;
+    virtual sph_status diagnostics(double out[8]) = 0;
+    virtual sph_status counters(int64_t* steps, int64_t* active) = 0;
+    virtual void grid(int32_t dims[3], int64_t* n_cells, double* cs) const = 0;
+    virtual sph_status profile(uint32_t mask) = 0;
+    virtual sph_status profile_read(double* ms, int64_t* timed, int64_t* launches) = 0;
+
+    std::string err;
+    cudaStream_t stream = nullptr;
+    bool dead = false;  // a sticky error happened
+};
+
+SimBase* make_sim_f32(cudaStream_t st);
+SimBase* make_sim_f64(cudaStream_t st);
+
+}  // namespace sph

@@ -1,0 +1,293 @@
+// Create-time kernels (binning from FP64 input, hydrostatic start, wall
+// normals), the FP64 state export and the FP64 diagnostics reductions.
+#pragma once
+
+#include "sph_kernels.cuh"
+
+namespace sph {
+
+// FP64 per-phase numbers used only at create time.
+struct InitCfg {
+    double lo[3];
+    double cs;
+    double gz;          // g_z (hydrostatic column along -z)
+    double c0, gamma;
+    int32_t n_phases;
+    int32_t has_rho;
+    double rho0[2], z_top[2];
+    int32_t eos[2];
+};
+
+// cell of an FP64 position: c = floor((x - lo)/cs) in FP64, offset x - lo - c cs
+// clamped into [0, cs] before rounding to T.
+template <class T>
+__device__ __forceinline__ void bin_fp64(const Cfg<T>& C, const InitCfg& I, const double* x,
+                                         int4& c, V4<T>& o)
+{
+    int32_t cc[3];
+    T oo[3];
+    for (int d = 0; d < 3; ++d) {
+        double u = x[d] - I.lo[d];
+        double f = floor(u / I.cs);
+        cc[d] = (f < -1e9) ? -1000000000 : (f > 1e9 ? 1000000000 : (int32_t)f);
+        double r = u - f * I.cs;
+        r = r < 0.0 ? 0.0 : (r > I.cs ? I.cs : r);
+        T rt = (T)r;
+        oo[d] = rt > C.cs ? C.cs : rt;
+    }
+    c = int4{cc[0], cc[1], cc[2], (int)cell_key(C, cc[0], cc[1], cc[2])};
+    o = V4<T>{oo[0], oo[1], oo[2], T(0)};
+}
+
+// hydrostatic pressure of stacked phase columns (phase k spans
+// (z_top[k-1], z_top[k]]), FP64
+__device__ __forceinline__ double hydro_p(const InitCfg& I, int k, double z)
+{
+    double g = -I.gz;
+    double p = I.rho0[k] * g * (I.z_top[k] - z);
+    for (int m = k + 1; m < I.n_phases; ++m) p += I.rho0[m] * g * (I.z_top[m] - I.z_top[m - 1]);
+    return p;
+}
+
+// Fluid in input order: cell, offset, velocity, density excess and pressure;
+// counts the cell occupancy for the first sort.
+template <class T>
+__global__ void k_init_fluid(Cfg<T> C, InitCfg I, int32_t n, const double* __restrict__ x,
+                             const double* __restrict__ v, const double* __restrict__ rho,
+                             const int32_t* __restrict__ phase_in, V4<T>* __restrict__ pos,
+                             V4<T>* __restrict__ vel, T* __restrict__ drho, V4<T>* __restrict__ acc,
+                             V4<T>* __restrict__ comp, int4* __restrict__ newcell,
+                             int32_t* __restrict__ id, int32_t* __restrict__ phase,
+                             int32_t* __restrict__ rank, int32_t* counts)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 c;
+    V4<T> o;
+    bin_fp64(C, I, x + 3 * i, c, o);
+    int ph = phase_in ? phase_in[i] : 0;
+    double d;
+    if (I.has_rho) {
+        d = rho[i] - I.rho0[ph];
+    } else {
+        double p = hydro_p(I, ph, x[3 * i + 2]);
+        if (I.eos[ph] == 1)
+            d = I.rho0[ph] * expm1(log1p(I.gamma * p / (I.rho0[ph] * I.c0 * I.c0)) / I.gamma);
+        else
+            d = p / (I.c0 * I.c0);
+    }
+    T dt = (T)d;
+    o.w = eos_p(C.ph[ph], C, dt);
+    pos[i] = o;
+    if (v)
+        vel[i] = V4<T>{(T)v[3 * i], (T)v[3 * i + 1], (T)v[3 * i + 2], C.ph[ph].rho0 + dt};
+    else
+        vel[i] = V4<T>{T(0), T(0), T(0), C.ph[ph].rho0 + dt};
+    drho[i] = dt;
+    acc[i] = V4<T>{T(0), T(0), T(0), T(0)};
+    comp[i] = V4<T>{T(0), T(0), T(0), T(0)};
+    newcell[i] = c;
+    id[i] = i;
+    phase[i] = ph;
+    int bucket = c.w < 0 ? C.n_cells : c.w;
+    rank[i] = atomicAdd(counts + bucket, 1);
+}
+
+// Walls in input order: cell, offset, counts.
+template <class T>
+__global__ void k_init_wall(Cfg<T> C, InitCfg I, int32_t n, const double* __restrict__ x,
+                            V4<T>* __restrict__ wpos, int4* __restrict__ wcell,
+                            int32_t* __restrict__ wid, int32_t* __restrict__ rank, int32_t* counts)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 c;
+    V4<T> o;
+    bin_fp64(C, I, x + 3 * i, c, o);
+    wpos[i] = o;
+    wcell[i] = c;
+    wid[i] = i;
+    int bucket = c.w < 0 ? C.n_cells : c.w;
+    rank[i] = atomicAdd(counts + bucket, 1);
+}
+
+// Walls into (key, id) order, with their FP64 positions for the normals.
+template <class T>
+__global__ void k_gather_wall(int32_t n, int32_t n_cells, const int32_t* __restrict__ start,
+                              const int32_t* __restrict__ tmp_src, const int32_t* __restrict__ tmp_id,
+                              const V4<T>* __restrict__ wpos, const int4* __restrict__ wcell,
+                              const double* __restrict__ x, V4<T>* __restrict__ wpos_o,
+                              int4* __restrict__ wcell_o, int32_t* __restrict__ wid_o,
+                              double* __restrict__ x_o)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int s = tmp_src[t];
+    int4 c = wcell[s];
+    int dst = sorted_slot(t, c.w, n_cells, start, tmp_id);
+    wpos_o[dst] = wpos[s];
+    wcell_o[dst] = c;
+    wid_o[dst] = tmp_id[t];
+    int id = tmp_id[t];
+    x_o[3 * dst] = x[3 * id];
+    x_o[3 * dst + 1] = x[3 * id + 1];
+    x_o[3 * dst + 2] = x[3 * id + 2];
+}
+
+// Wall unit normals, Eq. (normalVectors): n_w = Psi/|Psi|,
+// Psi = -sum_{j in wall} dx^3 grad_w W_wj, in FP64 from the FP64 positions
+// (exact lattice symmetry); |Psi| < 1e-6/dx gives n_w = 0.
+template <class T>
+__global__ void k_wall_normals(Cfg<double> D, int32_t n, const int32_t* __restrict__ wstart,
+                               const int4* __restrict__ wcell, const double* __restrict__ x,
+                               V4<T>* __restrict__ wnrm)
+{
+    int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= n) return;
+    int4 c = wcell[w];
+    double px = 0.0, py = 0.0, pz = 0.0;
+    const double xw = x[3 * w], yw = x[3 * w + 1], zw = x[3 * w + 2];
+    if (c.w >= 0) {
+        for_cells27(D, c.x, c.y, c.z, wstart, [&](int j, double, double, double) {
+            double rx = xw - x[3 * j], ry = yw - x[3 * j + 1], rz = zw - x[3 * j + 2];
+            double r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 >= D.rc2 || r2 == 0.0) return;
+            double F = kernel_F(D, sqrt(r2));
+            px -= D.dp3 * F * rx;
+            py -= D.dp3 * F * ry;
+            pz -= D.dp3 * F * rz;
+        });
+    }
+    double m = sqrt(px * px + py * py + pz * pz);
+    if (m >= 1e-6 * D.inv_dp)
+        wnrm[w] = V4<T>{(T)(px / m), (T)(py / m), (T)(pz / m), T(0)};
+    else
+        wnrm[w] = V4<T>{T(0), T(0), T(0), T(0)};
+}
+
+// ------------------------------------------------------------------ export
+struct ExportOut {
+    double *pos, *vel, *rho, *p, *acc, *drho_dt, *sigma;
+};
+
+template <class T>
+__global__ void k_export_fluid(Cfg<T> C, InitCfg I, int32_t n, const V4<T>* __restrict__ pos,
+                               const V4<T>* __restrict__ vel, const T* __restrict__ drho,
+                               const V4<T>* __restrict__ acc, const T* __restrict__ sigma,
+                               const int4* __restrict__ cell, const int32_t* __restrict__ id,
+                               const int32_t* __restrict__ phase, ExportOut o)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int i = id[k];
+    V4<T> p = pos[k], v = vel[k], a = acc[k];
+    int4 c = cell[k];
+    if (o.pos) {
+        o.pos[3 * i] = I.lo[0] + (double)c.x * I.cs + (double)p.x;
+        o.pos[3 * i + 1] = I.lo[1] + (double)c.y * I.cs + (double)p.y;
+        o.pos[3 * i + 2] = I.lo[2] + (double)c.z * I.cs + (double)p.z;
+    }
+    if (o.vel) {
+        o.vel[3 * i] = v.x;
+        o.vel[3 * i + 1] = v.y;
+        o.vel[3 * i + 2] = v.z;
+    }
+    if (o.rho) o.rho[i] = I.rho0[phase[k]] + (double)drho[k];
+    if (o.p) o.p[i] = p.w;
+    if (o.acc) {
+        o.acc[3 * i] = a.x;
+        o.acc[3 * i + 1] = a.y;
+        o.acc[3 * i + 2] = a.z;
+    }
+    if (o.drho_dt) o.drho_dt[i] = a.w;
+    if (o.sigma) o.sigma[i] = sigma[k];
+}
+
+template <class T>
+__global__ void k_export_wall(int32_t n, const V4<T>* __restrict__ wpos, const V2<T>* __restrict__ wrho,
+                              const V4<T>* __restrict__ wnrm, const int32_t* __restrict__ wid,
+                              double* pw, double* rhow, double* nrm)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int i = wid[k];
+    if (pw) pw[i] = wpos[k].w;
+    if (rhow) {
+        V2<T> r = wrho[k];
+        rhow[2 * i] = r.x;
+        rhow[2 * i + 1] = r.y;
+    }
+    if (nrm) {
+        V4<T> q = wnrm[k];
+        nrm[3 * i] = q.x;
+        nrm[3 * i + 1] = q.y;
+        nrm[3 * i + 2] = q.z;
+    }
+}
+
+// key per id and the sorted order, as the cell-list API returns them
+static __global__ void k_export_cells(int32_t n, const int4* __restrict__ cell,
+                                      const int32_t* __restrict__ id, uint32_t* __restrict__ key_by_id,
+                                      int32_t* __restrict__ order)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int i = id[k];
+    if (key_by_id) key_by_id[i] = (uint32_t)cell[k].w;
+    if (order) order[k] = i;
+}
+
+// ------------------------------------------------------------- diagnostics
+// FP64 block partials of {mass, momentum x/y/z, E_kin, E_pot, U_max, escaped};
+// a single block then sums them in a fixed order (deterministic).
+template <class T>
+__global__ void k_diag_partial(Cfg<T> C, InitCfg I, int32_t n, const V4<T>* __restrict__ pos,
+                               const V4<T>* __restrict__ vel, const int4* __restrict__ cell,
+                               const int32_t* __restrict__ phase, double* __restrict__ partial)
+{
+    __shared__ double sh[8][BLOCK];
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (k < n) {
+        V4<T> p = pos[k], v = vel[k];
+        int4 c = cell[k];
+        double m = (double)C.ph[phase[k]].m;
+        double vx = v.x, vy = v.y, vz = v.z;
+        double x = I.lo[0] + (double)c.x * I.cs + (double)p.x;
+        double y = I.lo[1] + (double)c.y * I.cs + (double)p.y;
+        double z = I.lo[2] + (double)c.z * I.cs + (double)p.z;
+        q[0] = m;
+        q[1] = m * vx;
+        q[2] = m * vy;
+        q[3] = m * vz;
+        q[4] = 0.5 * m * (vx * vx + vy * vy + vz * vz);
+        q[5] = -m * ((double)C.gx * x + (double)C.gy * y + (double)C.gz * z);
+        q[6] = c.w >= 0 ? sqrt(vx * vx + vy * vy + vz * vz) : 0.0;
+        q[7] = c.w >= 0 ? 0.0 : 1.0;
+    }
+    for (int f = 0; f < 8; ++f) sh[f][threadIdx.x] = q[f];
+    __syncthreads();
+    for (int s = BLOCK / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int f = 0; f < 8; ++f)
+                sh[f][threadIdx.x] = f == 6 ? fmax(sh[f][threadIdx.x], sh[f][threadIdx.x + s])
+                                            : sh[f][threadIdx.x] + sh[f][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) partial[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+static __global__ void k_diag_final(int32_t nblocks, const double* __restrict__ partial,
+                                    double* __restrict__ out)
+{
+    if (threadIdx.x >= 8) return;
+    int f = threadIdx.x;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        double v = partial[b * 8 + f];
+        s = f == 6 ? fmax(s, v) : s + v;
+    }
+    out[f] = s;
+}
+
+}  // namespace sph

@@ -1,0 +1,655 @@
+// Host-side orchestration of one simulation context: device buffers, the
+// create sequence and the kernel sequence of one step (Sec. 2.6, Sec. 3).
+// Included once per precision (sim_f32.cu, sim_f64.cu).
+#pragma once
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <type_traits>
+#include <utility>
+#include <vector>
+
+#include "sph_internal.h"
+#include "sph_setup.cuh"
+
+namespace sph {
+
+#define SPH_CUDA(call)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) return fail_cuda(e_, #call, __LINE__);                      \
+    } while (0)
+#define SPH_LAUNCH()                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ != cudaSuccess) return fail_cuda(e_, "kernel launch", __LINE__);            \
+    } while (0)
+
+// Launch one kernel (or a fixed group of nlaunch kernels) of a kind: counts
+// the launches and, when that kind is being profiled, brackets it with CUDA
+// events on the context's stream.
+#define SPH_KERNEL(kind, nlaunch, ...)                                                     \
+    do {                                                                                   \
+        sph_status ks_ = prof_begin(kind);                                                 \
+        if (ks_ != SPH_OK) return ks_;                                                     \
+        __VA_ARGS__;                                                                       \
+        SPH_LAUNCH();                                                                      \
+        launches_[kind] += (nlaunch);                                                      \
+        ks_ = prof_end(kind);                                                              \
+        if (ks_ != SPH_OK) return ks_;                                                     \
+    } while (0)
+
+inline int grid_for(int64_t n) { return (int)((n + BLOCK - 1) / BLOCK); }
+
+// number density of a full cubic lattice of spacing dp, self included
+inline double lattice_sigma0(double dp, double h)
+{
+    int K = (int)std::ceil(2.0 * h / dp) + 1;
+    const double pi = 3.14159265358979323846;
+    double alpha = 21.0 / (16.0 * pi * h * h * h), s = 0.0;
+    for (int i = -K; i <= K; ++i)
+        for (int j = -K; j <= K; ++j)
+            for (int k = -K; k <= K; ++k) {
+                double q = dp * std::sqrt((double)(i * i + j * j + k * k)) / h;
+                if (q < 2.0) {
+                    double t = 1.0 - 0.5 * q;
+                    s += alpha * t * t * t * t * (2.0 * q + 1.0);
+                }
+            }
+    return s;
+}
+
+template <class T>
+Cfg<T> make_cfg(const sph_params& P, const int32_t dims[3])
+{
+    const double pi = 3.14159265358979323846;
+    Cfg<T> C;
+    double h = P.h, cs = 2.0 * h;
+    double alpha = 21.0 / (16.0 * pi * h * h * h);
+    C.h = (T)h;
+    C.rc2 = (T)(cs * cs);
+    C.cs = (T)cs;
+    C.alpha = (T)alpha;
+    C.fcoef = (T)(-5.0 * alpha / (h * h));
+    C.W0 = (T)alpha;
+    C.inv_h = (T)(1.0 / h);
+    C.c0 = (T)P.c0;
+    C.inv_c0 = (T)(1.0 / P.c0);
+    C.gamma = (T)P.gamma_tait;
+    C.inv_gamma = (T)(1.0 / P.gamma_tait);
+    C.gamma_p = (T)P.gamma_p;
+    C.dp = (T)P.dp;
+    C.dp3 = (T)(P.dp * P.dp * P.dp);
+    C.inv_dp = (T)(1.0 / P.dp);
+    C.eta2 = (T)(0.01 * h * h);
+    C.pen_rmin = (T)(1e-6 * P.dp);
+    C.gx = (T)P.g[0];
+    C.gy = (T)P.g[1];
+    C.gz = (T)P.g[2];
+    C.inv_sigma0 = (T)(1.0 / lattice_sigma0(P.dp, h));
+    C.cfl = (T)P.cfl;
+    double gn = std::sqrt(P.g[0] * P.g[0] + P.g[1] * P.g[1] + P.g[2] * P.g[2]);
+    C.body_dt = gn > 0.0 ? (T)(P.cfl * std::sqrt(h / gn)) : T(0);
+    C.nx = dims[0];
+    C.ny = dims[1];
+    C.nz = dims[2];
+    C.n_cells = dims[0] * dims[1] * dims[2];
+    C.n_phases = P.n_phases;
+    for (int k = 0; k < 2; ++k) {
+        const sph_phase& ph = P.phase[k < P.n_phases ? k : 0];
+        PhaseK<T>& q = C.ph[k];
+        q.rho0 = (T)ph.rho0;
+        q.inv_rho0 = (T)(1.0 / ph.rho0);
+        q.mu = (T)ph.mu;
+        q.m = (T)(ph.rho0 * P.dp * P.dp * P.dp);
+        q.eos_k = ph.eos == SPH_EOS_TAIT ? (T)(ph.rho0 * P.c0 * P.c0 / P.gamma_tait) : (T)(P.c0 * P.c0);
+        q.eos = ph.eos;
+        q.density = ph.density;
+        q.reinit = ph.reinit;
+        q.penalty = ph.penalty;
+    }
+    return C;
+}
+
+template <class T>
+class Sim final : public SimBase {
+    static constexpr bool KAHAN = std::is_same<T, float>::value;
+
+  public:
+    explicit Sim(cudaStream_t st) { stream = st; }
+    ~Sim() override
+    {
+        for (void* p : allocs_) cudaFree(p);
+        for (EvPair& e : ev_) {
+            cudaEventDestroy(e.a);
+            cudaEventDestroy(e.b);
+        }
+        if (host_status_) cudaFreeHost(host_status_);
+    }
+
+    sph_status create(const sph_params& P, const sph_fluid& F, const sph_wall& Wl) override
+    {
+        P_ = P;
+        cs_ = 2.0 * P.h;
+        n_cells_ = 1;
+        for (int d = 0; d < 3; ++d) {
+            dims_[d] = (int32_t)std::ceil((P.hi[d] - P.lo[d]) / cs_);
+            if (dims_[d] < 1) dims_[d] = 1;
+            n_cells_ *= dims_[d];
+        }
+        C_ = make_cfg<T>(P, dims_);
+        D_ = make_cfg<double>(P, dims_);
+        for (int d = 0; d < 3; ++d) I_.lo[d] = P.lo[d];
+        I_.cs = cs_;
+        I_.gz = P.g[2];
+        I_.c0 = P.c0;
+        I_.gamma = P.gamma_tait;
+        I_.n_phases = P.n_phases;
+        I_.has_rho = F.rho != nullptr;
+        for (int k = 0; k < 2; ++k) {
+            const sph_phase& ph = P.phase[k < P.n_phases ? k : 0];
+            I_.rho0[k] = ph.rho0;
+            I_.z_top[k] = ph.z_top;
+            I_.eos[k] = ph.eos;
+        }
+        nf_ = (int32_t)F.n;
+        nw_ = (int32_t)Wl.n;
+        sph_status s = allocate();
+        if (s != SPH_OK) return s;
+        SPH_CUDA(cudaMallocHost(&host_status_, sizeof(HostStatus)));
+
+        // ---- walls: bin, sort once, normals (Eq. normalVectors)
+        double* xw_in = nullptr;
+        double* xw_sorted = nullptr;
+        if (nw_ > 0) {
+            SPH_CUDA(cudaMallocAsync(&xw_in, sizeof(double) * 3 * (size_t)nw_, stream));
+            SPH_CUDA(cudaMallocAsync(&xw_sorted, sizeof(double) * 3 * (size_t)nw_, stream));
+            SPH_CUDA(cudaMemcpyAsync(xw_in, Wl.pos, sizeof(double) * 3 * (size_t)nw_,
+                                     cudaMemcpyHostToDevice, stream));
+        }
+        SPH_CUDA(cudaMemsetAsync(counts_, 0, sizeof(int32_t) * (size_t)(n_cells_ + 1), stream));
+        if (nw_ > 0) {
+            k_init_wall<T><<<grid_for(nw_), BLOCK, 0, stream>>>(C_, I_, nw_, xw_in, wpos_tmp_, wcell_tmp_,
+                                                                wid_tmp_, rank_, counts_);
+            SPH_LAUNCH();
+        }
+        scan_exclusive(counts_, n_cells_ + 1, wstart_, sums_, stream);
+        SPH_LAUNCH();
+        if (nw_ > 0) {
+            k_scatter<<<grid_for(nw_), BLOCK, 0, stream>>>(nw_, n_cells_, wcell_tmp_, rank_, wstart_,
+                                                           wid_tmp_, tmp_src_, tmp_id_);
+            k_gather_wall<T><<<grid_for(nw_), BLOCK, 0, stream>>>(nw_, n_cells_, wstart_, tmp_src_, tmp_id_,
+                                                                  wpos_tmp_, wcell_tmp_, xw_in, wpos_, wcell_,
+                                                                  wid_, xw_sorted);
+            k_wall_normals<T><<<grid_for(nw_), BLOCK, 0, stream>>>(D_, nw_, wstart_, wcell_, xw_sorted, wnrm_);
+            SPH_LAUNCH();
+            SPH_CUDA(cudaFreeAsync(xw_in, stream));
+            SPH_CUDA(cudaFreeAsync(xw_sorted, stream));
+        }
+
+        // ---- fluid: upload, initial density, first sort
+        double *x_in = nullptr, *v_in = nullptr, *r_in = nullptr;
+        int32_t* ph_in = nullptr;
+        if (nf_ > 0) {
+            size_t b3 = sizeof(double) * 3 * (size_t)nf_;
+            SPH_CUDA(cudaMallocAsync(&x_in, b3, stream));
+            SPH_CUDA(cudaMemcpyAsync(x_in, F.pos, b3, cudaMemcpyHostToDevice, stream));
+            if (F.vel) {
+                SPH_CUDA(cudaMallocAsync(&v_in, b3, stream));
+                SPH_CUDA(cudaMemcpyAsync(v_in, F.vel, b3, cudaMemcpyHostToDevice, stream));
+            }
+            if (F.rho) {
+                SPH_CUDA(cudaMallocAsync(&r_in, sizeof(double) * (size_t)nf_, stream));
+                SPH_CUDA(cudaMemcpyAsync(r_in, F.rho, sizeof(double) * (size_t)nf_, cudaMemcpyHostToDevice,
+                                         stream));
+            }
+            if (F.phase) {
+                SPH_CUDA(cudaMallocAsync(&ph_in, sizeof(int32_t) * (size_t)nf_, stream));
+                SPH_CUDA(cudaMemcpyAsync(ph_in, F.phase, sizeof(int32_t) * (size_t)nf_,
+                                         cudaMemcpyHostToDevice, stream));
+            }
+        }
+        SPH_CUDA(cudaMemsetAsync(counts_, 0, sizeof(int32_t) * (size_t)(n_cells_ + 1), stream));
+        SPH_CUDA(cudaMemsetAsync(d_dt_, 0, sizeof(T), stream));
+        SPH_CUDA(cudaMemsetAsync(d_dt_fixed_, 0, sizeof(T), stream));
+        SPH_CUDA(cudaMemsetAsync(d_vmax_, 0, sizeof(unsigned long long), stream));
+        SPH_CUDA(cudaMemsetAsync(d_flags_, 0, sizeof(int32_t), stream));
+        SPH_CUDA(cudaMemsetAsync(d_active_, 0, sizeof(unsigned long long), stream));
+        par_ = 0;
+        if (nf_ > 0) {
+            k_init_fluid<T><<<grid_for(nf_), BLOCK, 0, stream>>>(
+                C_, I_, nf_, x_in, v_in, r_in, ph_in, pos_[0], vel_[0], drho_[0], acc_, comp_[0], newcell_,
+                id_[0], phase_[0], rank_, counts_);
+            SPH_LAUNCH();
+        }
+        scan_exclusive(counts_, n_cells_ + 1, fstart_, sums_, stream);
+        SPH_LAUNCH();
+        if (nf_ > 0) {
+            k_scatter<<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, n_cells_, newcell_, rank_, fstart_, id_[0],
+                                                           tmp_src_, tmp_id_);
+            // dt = 0 and no reinitialisation: a pure permutation into (key, id) order
+            k_gather<T, KAHAN><<<grid_for(nf_), BLOCK, 0, stream>>>(
+                C_, nf_, fstart_, tmp_src_, tmp_id_, newcell_, d_dt_, 0, pos_[0], vel_[0], drho_[0], acc_,
+                comp_[0], sigma_, newcell_, phase_[0], pos_[1], vel_[1], drho_[1], comp_[1], cell_[1], id_[1],
+                phase_[1]);
+            SPH_LAUNCH();
+            for (void* p : {(void*)x_in, (void*)v_in, (void*)r_in, (void*)ph_in})
+                if (p) SPH_CUDA(cudaFreeAsync(p, stream));
+        }
+        // the sorted state is in the [1] buffers; make it current
+        std::swap(pos_[0], pos_[1]);
+        std::swap(drho_[0], drho_[1]);
+        par_ = 1;
+
+        // ---- wall pressure of the initial state, then a^0, sigma^0, U_max
+        s = wall_pressure(vel_[1]);
+        if (s != SPH_OK) return s;
+        s = momentum(vel_[1], vel_[0], cell_[1], phase_[1]);  // dt = 0: writes v + 0*a
+        if (s != SPH_OK) return s;
+        std::swap(vel_[0], vel_[1]);
+
+        SPH_CUDA(cudaMemcpyAsync(&host_status_->n_in, fstart_ + n_cells_, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaMemcpyAsync(&host_status_->w_in, wstart_ + n_cells_, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        if (host_status_->n_in != nf_ || host_status_->w_in != nw_) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "%d fluid and %d wall particles lie outside the grid [lo, hi)",
+                     nf_ - host_status_->n_in, nw_ - host_status_->w_in);
+            err = buf;
+            return SPH_ERR_DOMAIN;
+        }
+        return SPH_OK;
+    }
+
+    sph_status step(int32_t nsteps, double dt, double* dt_out) override
+    {
+        // pinned source; the previous call's copy has completed (each call ends
+        // with a stream synchronisation)
+        host_status_->dt_fixed = (T)(dt > 0.0 ? dt : 0.0);
+        SPH_CUDA(cudaMemcpyAsync(d_dt_fixed_, &host_status_->dt_fixed, sizeof(T), cudaMemcpyHostToDevice,
+                                 stream));
+        for (int32_t k = 0; k < nsteps; ++k) {
+            bool reinit = P_.reinit_every > 0 && (steps_ % P_.reinit_every) == 0;
+            sph_status s = one_step(reinit);
+            if (s != SPH_OK) return s;
+            ++steps_;
+        }
+        SPH_CUDA(cudaMemcpyAsync(&host_status_->flags, d_flags_, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 stream));
+        SPH_CUDA(cudaMemcpyAsync(&host_status_->n_in, fstart_ + n_cells_, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaMemcpyAsync(&host_status_->dt, d_dt_, sizeof(T), cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        if (dt_out) *dt_out = (double)host_status_->dt;
+        if (host_status_->flags & 1) {
+            err = "non-finite acceleration";
+            dead = true;
+            return SPH_ERR_NONFINITE;
+        }
+        if (host_status_->n_in != nf_) {
+            char buf[96];
+            snprintf(buf, sizeof buf, "%d fluid particles outside the grid", nf_ - host_status_->n_in);
+            err = buf;
+            return SPH_ERR_DOMAIN;
+        }
+        return SPH_OK;
+    }
+
+    sph_status reinit() override
+    {
+        if (nf_ > 0)
+            SPH_KERNEL(SPH_K_OTHER, 1,
+                       k_reinit<T><<<grid_for(nf_), BLOCK, 0, stream>>>(C_, nf_, sigma_, cell_[par_], phase_[par_],
+                                                                        pos_[0], vel_[par_], drho_[0]));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        return SPH_OK;
+    }
+
+    sph_status profile(uint32_t mask) override
+    {
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        prof_mask_ = mask;
+        ev_used_ = 0;
+        return SPH_OK;
+    }
+
+    sph_status profile_read(double* ms, int64_t* timed, int64_t* launches) override
+    {
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        double acc_ms[SPH_NK] = {0};
+        int64_t cnt[SPH_NK] = {0};
+        for (size_t k = 0; k < ev_used_; ++k) {
+            float t = 0.f;
+            SPH_CUDA(cudaEventElapsedTime(&t, ev_[k].a, ev_[k].b));
+            acc_ms[ev_[k].kind] += t;
+            cnt[ev_[k].kind] += 1;
+        }
+        for (int k = 0; k < SPH_NK; ++k) {
+            if (ms) ms[k] = acc_ms[k];
+            if (timed) timed[k] = cnt[k];
+            if (launches) launches[k] = launches_[k];
+        }
+        return SPH_OK;
+    }
+
+    sph_status get_state(const sph_state_out& o, int32_t where) override
+    {
+        const bool host = where == SPH_HOST;
+        const size_t n1 = sizeof(double) * (size_t)nf_, n3 = 3 * n1;
+        const size_t w1 = sizeof(double) * (size_t)nw_;
+        struct Req {
+            double* user;
+            size_t bytes;
+            double* dev;
+        };
+        Req req[10] = {{o.pos, n3, nullptr},    {o.vel, n3, nullptr},     {o.rho, n1, nullptr},
+                       {o.p, n1, nullptr},      {o.acc, n3, nullptr},     {o.drho_dt, n1, nullptr},
+                       {o.sigma, n1, nullptr},  {o.pw, w1, nullptr},      {o.rhow, 2 * w1, nullptr},
+                       {o.normal, 3 * w1, nullptr}};
+        for (Req& r : req) {
+            if (!r.user || r.bytes == 0) continue;
+            if (host)
+                SPH_CUDA(cudaMallocAsync(&r.dev, r.bytes, stream));
+            else
+                r.dev = r.user;
+        }
+        if (nf_ > 0) {
+            ExportOut eo{req[0].dev, req[1].dev, req[2].dev, req[3].dev, req[4].dev, req[5].dev, req[6].dev};
+            k_export_fluid<T><<<grid_for(nf_), BLOCK, 0, stream>>>(C_, I_, nf_, pos_[0], vel_[par_], drho_[0], acc_,
+                                                                 sigma_, cell_[par_], id_[par_], phase_[par_],
+                                                                 eo);
+            SPH_LAUNCH();
+        }
+        if (nw_ > 0) {
+            k_export_wall<T><<<grid_for(nw_), BLOCK, 0, stream>>>(nw_, wpos_, wrho_, wnrm_, wid_, req[7].dev,
+                                                                req[8].dev, req[9].dev);
+            SPH_LAUNCH();
+        }
+        if (host) {
+            for (Req& r : req) {
+                if (!r.dev) continue;
+                SPH_CUDA(cudaMemcpyAsync(r.user, r.dev, r.bytes, cudaMemcpyDeviceToHost, stream));
+                SPH_CUDA(cudaFreeAsync(r.dev, stream));
+            }
+        }
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        return SPH_OK;
+    }
+
+    sph_status get_cells(uint32_t* kf, int32_t* of, int32_t* sf, uint32_t* kw, int32_t* ow,
+                         int32_t* sw) override
+    {
+        uint32_t* dk = nullptr;
+        int32_t* dord = nullptr;
+        size_t nmax = (size_t)(nf_ > nw_ ? nf_ : nw_);
+        if (nmax > 0) {
+            SPH_CUDA(cudaMallocAsync(&dk, sizeof(uint32_t) * nmax, stream));
+            SPH_CUDA(cudaMallocAsync(&dord, sizeof(int32_t) * nmax, stream));
+        }
+        if ((kf || of) && nf_ > 0) {
+            k_export_cells<<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, cell_[par_], id_[par_], dk, dord);
+            SPH_LAUNCH();
+            if (kf) SPH_CUDA(cudaMemcpyAsync(kf, dk, sizeof(uint32_t) * nf_, cudaMemcpyDeviceToHost, stream));
+            if (of) SPH_CUDA(cudaMemcpyAsync(of, dord, sizeof(int32_t) * nf_, cudaMemcpyDeviceToHost, stream));
+            SPH_CUDA(cudaStreamSynchronize(stream));
+        }
+        if (sf)
+            SPH_CUDA(cudaMemcpyAsync(sf, fstart_, sizeof(int32_t) * (size_t)(n_cells_ + 1),
+                                     cudaMemcpyDeviceToHost, stream));
+        if ((kw || ow) && nw_ > 0) {
+            k_export_cells<<<grid_for(nw_), BLOCK, 0, stream>>>(nw_, wcell_, wid_, dk, dord);
+            SPH_LAUNCH();
+            if (kw) SPH_CUDA(cudaMemcpyAsync(kw, dk, sizeof(uint32_t) * nw_, cudaMemcpyDeviceToHost, stream));
+            if (ow) SPH_CUDA(cudaMemcpyAsync(ow, dord, sizeof(int32_t) * nw_, cudaMemcpyDeviceToHost, stream));
+        }
+        if (sw)
+            SPH_CUDA(cudaMemcpyAsync(sw, wstart_, sizeof(int32_t) * (size_t)(n_cells_ + 1),
+                                     cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        if (dk) SPH_CUDA(cudaFreeAsync(dk, stream));
+        if (dord) SPH_CUDA(cudaFreeAsync(dord, stream));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        return SPH_OK;
+    }
+
+    sph_status diagnostics(double out[8]) override
+    {
+        int nb = grid_for(nf_ > 0 ? nf_ : 1);
+        k_diag_partial<T><<<nb, BLOCK, 0, stream>>>(C_, I_, nf_, pos_[0], vel_[par_], cell_[par_], phase_[par_],
+                                                    diag_partial_);
+        k_diag_final<<<1, 32, 0, stream>>>(nb, diag_partial_, diag_out_);
+        SPH_LAUNCH();
+        SPH_CUDA(cudaMemcpyAsync(host_status_->diag, diag_out_, sizeof(double) * 8, cudaMemcpyDeviceToHost,
+                                 stream));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        memcpy(out, host_status_->diag, sizeof(double) * 8);
+        return SPH_OK;
+    }
+
+    sph_status counters(int64_t* steps, int64_t* active) override
+    {
+        SPH_CUDA(cudaMemcpyAsync(&host_status_->active, d_active_, sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        if (steps) *steps = steps_;
+        if (active) *active = (int64_t)host_status_->active;
+        return SPH_OK;
+    }
+
+    void grid(int32_t dims[3], int64_t* n_cells, double* cs) const override
+    {
+        if (dims)
+            for (int d = 0; d < 3; ++d) dims[d] = dims_[d];
+        if (n_cells) *n_cells = n_cells_;
+        if (cs) *cs = cs_;
+    }
+
+  private:
+    struct HostStatus {
+        int32_t flags, n_in, w_in, pad;
+        T dt, dt_fixed;
+        unsigned long long active;
+        double diag[8];
+    };
+    struct EvPair {
+        cudaEvent_t a, b;
+        int kind;
+    };
+    static constexpr size_t kMaxEvents = 1u << 18;
+
+    sph_status fail_cuda(cudaError_t e, const char* what, int line)
+    {
+        char buf[256];
+        snprintf(buf, sizeof buf, "CUDA error %s (%s) at %s [sph_sim.cuh:%d]", cudaGetErrorName(e),
+                 cudaGetErrorString(e), what, line);
+        err = buf;
+        dead = true;
+        return e == cudaErrorMemoryAllocation ? SPH_ERR_OOM : SPH_ERR_CUDA;
+    }
+
+    template <class U>
+    sph_status alloc(U*& p, size_t count)
+    {
+        p = nullptr;
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void**)&p, sizeof(U) * count);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc", __LINE__);
+        allocs_.push_back((void*)p);
+        return SPH_OK;
+    }
+
+    sph_status allocate()
+    {
+        size_t nf = (size_t)nf_, nw = (size_t)nw_, nc = (size_t)n_cells_;
+        size_t nmax = nf > nw ? nf : nw;
+        sph_status s = SPH_OK;
+        for (int b = 0; b < 2 && s == SPH_OK; ++b) {
+            if ((s = alloc(pos_[b], nf)) != SPH_OK) return s;
+            if ((s = alloc(vel_[b], nf)) != SPH_OK) return s;
+            if ((s = alloc(drho_[b], nf)) != SPH_OK) return s;
+            if ((s = alloc(comp_[b], nf)) != SPH_OK) return s;
+            if ((s = alloc(cell_[b], nf)) != SPH_OK) return s;
+            if ((s = alloc(id_[b], nf)) != SPH_OK) return s;
+            if ((s = alloc(phase_[b], nf)) != SPH_OK) return s;
+        }
+        if ((s = alloc(acc_, nf)) != SPH_OK) return s;
+        if ((s = alloc(sigma_, nf)) != SPH_OK) return s;
+        if ((s = alloc(newcell_, nmax)) != SPH_OK) return s;
+        if ((s = alloc(rank_, nmax)) != SPH_OK) return s;
+        if ((s = alloc(tmp_src_, nmax)) != SPH_OK) return s;
+        if ((s = alloc(tmp_id_, nmax)) != SPH_OK) return s;
+        if ((s = alloc(counts_, nc + 1)) != SPH_OK) return s;
+        if ((s = alloc(fstart_, nc + 2)) != SPH_OK) return s;
+        if ((s = alloc(wstart_, nc + 2)) != SPH_OK) return s;
+        if ((s = alloc(sums_, (size_t)scan_blocks(n_cells_ + 1))) != SPH_OK) return s;
+        if ((s = alloc(wpos_, nw)) != SPH_OK) return s;
+        if ((s = alloc(wpos_tmp_, nw)) != SPH_OK) return s;
+        if ((s = alloc(wrho_, nw)) != SPH_OK) return s;
+        if ((s = alloc(wnrm_, nw)) != SPH_OK) return s;
+        if ((s = alloc(wcell_, nw)) != SPH_OK) return s;
+        if ((s = alloc(wcell_tmp_, nw)) != SPH_OK) return s;
+        if ((s = alloc(wid_, nw)) != SPH_OK) return s;
+        if ((s = alloc(wid_tmp_, nw)) != SPH_OK) return s;
+        if ((s = alloc(d_dt_, 1)) != SPH_OK) return s;
+        if ((s = alloc(d_dt_fixed_, 1)) != SPH_OK) return s;
+        if ((s = alloc(d_vmax_, 1)) != SPH_OK) return s;
+        if ((s = alloc(d_flags_, 1)) != SPH_OK) return s;
+        if ((s = alloc(d_active_, 1)) != SPH_OK) return s;
+        if ((s = alloc(diag_partial_, 8 * (size_t)grid_for(nf_ > 0 ? nf_ : 1))) != SPH_OK) return s;
+        if ((s = alloc(diag_out_, 8)) != SPH_OK) return s;
+        return SPH_OK;
+    }
+
+    // Eq. (wallPressure) from the fluid state pos[0] / vel_cur
+    sph_status wall_pressure(const V4<T>* vel_cur)
+    {
+        if (nw_ == 0) return SPH_OK;
+        SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
+                   k_wall_pressure<T><<<grid_for(nw_), BLOCK, 0, stream>>>(C_, nw_, fstart_, wpos_, wcell_, pos_[0],
+                                                                           vel_cur, wrho_, d_active_));
+        return SPH_OK;
+    }
+
+    // momentum from pos[0] / vel_cur; writes acc, vel_out (final kick),
+    // sigma and U_max
+    sph_status momentum(const V4<T>* vel_cur, V4<T>* vel_out, const int4* cell, const int32_t* phase)
+    {
+        if (nf_ == 0) return SPH_OK;
+        SPH_KERNEL(SPH_K_MOMENTUM, 1,
+                   k_momentum<T><<<grid_for(nf_), BLOCK, 0, stream>>>(C_, nf_, fstart_, wstart_, pos_[0], vel_cur,
+                                                                      cell, phase, wpos_, wrho_, wnrm_, d_dt_, acc_,
+                                                                      vel_out, sigma_, d_vmax_, d_flags_));
+        return SPH_OK;
+    }
+
+    // One kick-drift-kick step (Sec. 2.6).  Buffer roles with p = par_, q = p^1:
+    //   gather    : pos[0], vel[p], drho[0], comp/cell/id/phase[p] (old order)
+    //               -> pos[1], vel[q], drho[1], comp/cell/id/phase[q] (new order)
+    //   continuity: pos[1], vel[q], drho[1] -> pos[0], vel[p], drho[0], acc.w
+    //   wall pressure, momentum read pos[0], vel[p]; momentum writes vel[q]
+    // so pos and drho stay in [0] while vel, comp, cell, id, phase alternate.
+    sph_status one_step(bool reinit)
+    {
+        const int p = par_, q = par_ ^ 1;
+        SPH_KERNEL(SPH_K_BEGIN_STEP, 1,
+                   k_begin_step<T><<<grid_for(n_cells_ + 1), BLOCK, 0, stream>>>(C_, d_dt_fixed_, d_vmax_, d_dt_,
+                                                                                counts_, n_cells_ + 1));
+        if (nf_ > 0)
+            SPH_KERNEL(SPH_K_PREDICT, 1,
+                       k_predict<T, KAHAN><<<grid_for(nf_), BLOCK, 0, stream>>>(
+                           C_, nf_, pos_[0], vel_[p], acc_, comp_[p], cell_[p], d_dt_, newcell_, rank_, counts_));
+        SPH_KERNEL(SPH_K_SCAN, 3, scan_exclusive(counts_, n_cells_ + 1, fstart_, sums_, stream));
+        if (nf_ > 0) {
+            SPH_KERNEL(SPH_K_SCATTER, 1,
+                       k_scatter<<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, n_cells_, newcell_, rank_, fstart_,
+                                                                      id_[p], tmp_src_, tmp_id_));
+            SPH_KERNEL(SPH_K_GATHER, 1,
+                       k_gather<T, KAHAN><<<grid_for(nf_), BLOCK, 0, stream>>>(
+                           C_, nf_, fstart_, tmp_src_, tmp_id_, newcell_, d_dt_, reinit ? 1 : 0, pos_[0], vel_[p],
+                           drho_[0], acc_, comp_[p], sigma_, cell_[p], phase_[p], pos_[1], vel_[q], drho_[1],
+                           comp_[q], cell_[q], id_[q], phase_[q]));
+            SPH_KERNEL(SPH_K_CONTINUITY, 1,
+                       k_continuity<T><<<grid_for(nf_), BLOCK, 0, stream>>>(
+                           C_, nf_, fstart_, wstart_, pos_[1], vel_[q], drho_[1], cell_[q], phase_[q], wpos_,
+                           wrho_, d_dt_, pos_[0], vel_[p], drho_[0], acc_));
+        }
+        sph_status s = wall_pressure(vel_[p]);
+        if (s != SPH_OK) return s;
+        s = momentum(vel_[p], vel_[q], cell_[q], phase_[q]);
+        if (s != SPH_OK) return s;
+        par_ = q;
+        return SPH_OK;
+    }
+
+    sph_status prof_begin(int kind)
+    {
+        if (!((prof_mask_ >> kind) & 1u) || ev_used_ >= kMaxEvents) return SPH_OK;
+        if (ev_used_ == ev_.size()) {
+            EvPair e{nullptr, nullptr, 0};
+            SPH_CUDA(cudaEventCreate(&e.a));
+            SPH_CUDA(cudaEventCreate(&e.b));
+            ev_.push_back(e);
+        }
+        ev_[ev_used_].kind = kind;
+        SPH_CUDA(cudaEventRecord(ev_[ev_used_].a, stream));
+        prof_open_ = true;
+        return SPH_OK;
+    }
+
+    sph_status prof_end(int kind)
+    {
+        (void)kind;
+        if (!prof_open_) return SPH_OK;
+        SPH_CUDA(cudaEventRecord(ev_[ev_used_].b, stream));
+        ++ev_used_;
+        prof_open_ = false;
+        return SPH_OK;
+    }
+
+    sph_params P_{};
+    Cfg<T> C_{};
+    Cfg<double> D_{};
+    InitCfg I_{};
+    int32_t nf_ = 0, nw_ = 0, n_cells_ = 0, dims_[3] = {1, 1, 1};
+    double cs_ = 0.0;
+    int par_ = 0;
+    int64_t steps_ = 0;
+
+    V4<T>* pos_[2] = {nullptr, nullptr};
+    V4<T>* vel_[2] = {nullptr, nullptr};
+    T* drho_[2] = {nullptr, nullptr};
+    V4<T>* comp_[2] = {nullptr, nullptr};
+    int4* cell_[2] = {nullptr, nullptr};
+    int32_t* id_[2] = {nullptr, nullptr};
+    int32_t* phase_[2] = {nullptr, nullptr};
+    V4<T>* acc_ = nullptr;
+    T* sigma_ = nullptr;
+    int4* newcell_ = nullptr;
+    int32_t *rank_ = nullptr, *tmp_src_ = nullptr, *tmp_id_ = nullptr;
+    int32_t *counts_ = nullptr, *fstart_ = nullptr, *wstart_ = nullptr, *sums_ = nullptr;
+    V4<T>* wpos_ = nullptr;
+    V4<T>* wpos_tmp_ = nullptr;
+    V2<T>* wrho_ = nullptr;
+    V4<T>* wnrm_ = nullptr;
+    int4 *wcell_ = nullptr, *wcell_tmp_ = nullptr;
+    int32_t *wid_ = nullptr, *wid_tmp_ = nullptr;
+    T* d_dt_ = nullptr;
+    T* d_dt_fixed_ = nullptr;
+    unsigned long long* d_vmax_ = nullptr;
+    int32_t* d_flags_ = nullptr;
+    unsigned long long* d_active_ = nullptr;
+    double* diag_partial_ = nullptr;
+    double* diag_out_ = nullptr;
+    HostStatus* host_status_ = nullptr;
+    std::vector<void*> allocs_;
+    uint32_t prof_mask_ = 0;
+    bool prof_open_ = false;
+    int64_t launches_[SPH_NK] = {0};
+    std::vector<EvPair> ev_;
+    size_t ev_used_ = 0;
+};
+
+}  // namespace sph

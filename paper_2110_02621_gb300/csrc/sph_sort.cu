@@ -1,0 +1,187 @@
+// Counting sort of particles by cell key (Sec. 3, "neighbour search
+// including sorting"): exclusive scan of the per-cell counts, first
+// placement by arrival rank, then the in-cell rank by particle id makes the
+// final order (key, id) independent of atomic arrival order.  The scan is a
+// three-kernel reduce / scan-of-sums / down-sweep with no inter-block waits.
+#include <cstdint>
+#include <cstdio>
+
+#include "sph_internal.h"
+#include "sph_setup.cuh"
+
+namespace sph {
+
+constexpr int SCAN_THREADS = 512;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 4096 values per block
+
+__device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* total)
+{
+    __shared__ int32_t warp_sums[SCAN_THREADS / 32];
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < SCAN_THREADS / 32) warp_sums[lane] = w;
+    }
+    __syncthreads();
+    int32_t before = warp > 0 ? warp_sums[warp - 1] : 0;
+    *total = warp_sums[SCAN_THREADS / 32 - 1];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int32_t* __restrict__ in, int32_t n,
+                                                              int32_t* __restrict__ sums)
+{
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int32_t s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < n) s += in[base + k];
+    int32_t total;
+    block_exclusive_scan(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// one block: exclusive scan of the block sums (at most SCAN_TILE of them)
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int32_t* sums, int32_t nb)
+{
+    int base = threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS], s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < nb ? sums[base + k] : 0;
+        s += v[k];
+    }
+    int32_t total;
+    int32_t off = block_exclusive_scan(s, &total);
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < nb) sums[base + k] = off;
+        off += v[k];
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int32_t* __restrict__ in, int32_t n,
+                                                            const int32_t* __restrict__ sums,
+                                                            int32_t* __restrict__ out)
+{
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS], s = 0;
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    int32_t total;
+    int32_t off = block_exclusive_scan(s, &total) + sums[blockIdx.x];
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) out[base + k] = off;
+        off += v[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) out[n] = off;
+}
+
+int32_t scan_blocks(int64_t n) { return (int32_t)((n + SCAN_TILE - 1) / SCAN_TILE); }
+int64_t scan_max_len() { return (int64_t)SCAN_TILE * SCAN_TILE; }
+
+void scan_exclusive(const int32_t* in, int32_t n, int32_t* out, int32_t* sums, cudaStream_t st)
+{
+    int nb = scan_blocks(n);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(in, n, sums);
+    k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(sums, nb);
+    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(in, n, sums, out);
+}
+
+// ------------------------------------------------- stand-alone binning API
+__global__ void k_bin_keys(int32_t n, const double* __restrict__ x, double lo0, double lo1, double lo2,
+                           double cs, int32_t nx, int32_t ny, int32_t nz, int4* __restrict__ cell,
+                           int32_t* __restrict__ id, int32_t* __restrict__ rank, int32_t* counts,
+                           int32_t n_cells)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double lo[3] = {lo0, lo1, lo2};
+    int32_t dims[3] = {nx, ny, nz}, c[3];
+    bool inside = true;
+    for (int d = 0; d < 3; ++d) {
+        double f = floor((x[3 * i + d] - lo[d]) / cs);
+        c[d] = (f < -1e9) ? -1000000000 : (f > 1e9 ? 1000000000 : (int32_t)f);
+        inside = inside && c[d] >= 0 && c[d] < dims[d];
+    }
+    int key = inside ? (c[2] * ny + c[1]) * nx + c[0] : -1;
+    cell[i] = int4{c[0], c[1], c[2], key};
+    id[i] = i;
+    rank[i] = atomicAdd(counts + (key < 0 ? n_cells : key), 1);
+}
+
+__global__ void k_bin_order(int32_t n, int32_t n_cells, const int32_t* __restrict__ start,
+                            const int32_t* __restrict__ tmp_src, const int32_t* __restrict__ tmp_id,
+                            const int4* __restrict__ cell, uint32_t* __restrict__ key_by_id,
+                            int32_t* __restrict__ order)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    int s = tmp_src[t];
+    int key = cell[s].w;
+    int dst = sorted_slot(t, key, n_cells, start, tmp_id);
+    order[dst] = tmp_id[t];
+    key_by_id[tmp_id[t]] = (uint32_t)key;
+}
+
+BinSortScratch bin_sort_scratch_layout(int64_t n, int64_t n_cells)
+{
+    BinSortScratch L;
+    auto up = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t off = 0;
+    L.cell = off; off += up(sizeof(int4) * (size_t)n);
+    L.id = off; off += up(sizeof(int32_t) * (size_t)n);
+    L.rank = off; off += up(sizeof(int32_t) * (size_t)n);
+    L.tmp_src = off; off += up(sizeof(int32_t) * (size_t)n);
+    L.tmp_id = off; off += up(sizeof(int32_t) * (size_t)n);
+    L.counts = off; off += up(sizeof(int32_t) * (size_t)(n_cells + 1));
+    L.start = off; off += up(sizeof(int32_t) * (size_t)(n_cells + 2));
+    L.sums = off; off += up(sizeof(int32_t) * (size_t)scan_blocks(n_cells + 1));
+    L.bytes = off;
+    return L;
+}
+
+cudaError_t bin_sort_run(const double* pos, int32_t n, const double lo[3], double cs,
+                         const int32_t dims[3], uint32_t* key, int32_t* order, int32_t* start,
+                         char* scratch, cudaStream_t st)
+{
+    int32_t n_cells = dims[0] * dims[1] * dims[2];
+    BinSortScratch L = bin_sort_scratch_layout(n, n_cells);
+    int4* cell = (int4*)(scratch + L.cell);
+    int32_t* id = (int32_t*)(scratch + L.id);
+    int32_t* rank = (int32_t*)(scratch + L.rank);
+    int32_t* tmp_src = (int32_t*)(scratch + L.tmp_src);
+    int32_t* tmp_id = (int32_t*)(scratch + L.tmp_id);
+    int32_t* counts = (int32_t*)(scratch + L.counts);
+    int32_t* fullstart = (int32_t*)(scratch + L.start);
+    int32_t* sums = (int32_t*)(scratch + L.sums);
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)(n_cells + 1), st);
+    if (e != cudaSuccess) return e;
+    int nb = (n + BLOCK - 1) / BLOCK;
+    if (n > 0)
+        k_bin_keys<<<nb, BLOCK, 0, st>>>(n, pos, lo[0], lo[1], lo[2], cs, dims[0], dims[1], dims[2],
+                                         cell, id, rank, counts, n_cells);
+    scan_exclusive(counts, n_cells + 1, fullstart, sums, st);
+    if (n > 0) {
+        k_scatter<<<nb, BLOCK, 0, st>>>(n, n_cells, cell, rank, fullstart, id, tmp_src, tmp_id);
+        k_bin_order<<<nb, BLOCK, 0, st>>>(n, n_cells, fullstart, tmp_src, tmp_id, cell, key, order);
+    }
+    e = cudaMemcpyAsync(start, fullstart, sizeof(int32_t) * (size_t)(n_cells + 1),
+                        cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace sph

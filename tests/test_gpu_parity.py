@@ -1,0 +1,288 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the method's required accuracy):
+  * cell keys, sorted order, cell ranges: bit-exact;
+  * single-step accelerations and density rates: ||gpu - ref||_inf / ||ref||_inf
+    <= 2e-5 per field (a per-particle relative error is meaningless near
+    hydrostatic balance, where a ~ 0);
+  * trajectories: |x_gpu - x_ref| <= 1e-3 dp after up to 100 steps;
+  * the plain FP64 form: the same fields within 1e-9.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_02621_gb300 import build, scenes as S, sph
+
+pytestmark = pytest.mark.gpu
+
+TOL_RATE = 2e-5
+TOL_X = 1e-3
+TOL_FP64 = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    oracle.build()
+    sph.lib()
+
+
+def rel_inf(g, r):
+    g, r = np.asarray(g), np.asarray(r)
+    den = np.abs(r).max()
+    return float(np.abs(g - r).max() / den) if den > 0 else float(np.abs(g).max())
+
+
+def small_dam(**kw):
+    return S.dam_break(tank=(0.3, 0.12, 0.15), column=(0.1, 0.12, 0.08), dp=0.01, **kw)
+
+
+def check_cells(sim, ref, n_in_only=False):
+    g, o = sim.cells(), ref.cells()
+    assert np.array_equal(g["dims"], o["dims"])
+    assert np.array_equal(g["key_f"], o["key_f"])
+    assert np.array_equal(g["start_f"], o["start_f"].astype(np.int32))
+    n_in = int(o["start_f"][-1])
+    assert np.array_equal(g["order_f"][:n_in], o["order_f"][:n_in].astype(np.int32))
+    assert np.array_equal(g["key_w"], o["key_w"])
+    assert np.array_equal(g["order_w"], o["order_w"].astype(np.int32))
+    assert np.array_equal(g["start_w"], o["start_w"].astype(np.int32))
+
+
+def check_state(g, o, ow, dp, tol_rate=TOL_RATE, tol_x=TOL_X, what=""):
+    assert np.abs(g["x"] - o["x"]).max() <= tol_x * dp, what
+    assert rel_inf(g["a"], o["a"]) <= tol_rate, (what, rel_inf(g["a"], o["a"]))
+    assert rel_inf(g["drho_dt"], o["drho_dt"]) <= tol_rate, (what, rel_inf(g["drho_dt"], o["drho_dt"]))
+    assert rel_inf(g["rho"], o["rho"]) <= tol_rate, what
+    assert rel_inf(g["p"], o["p"]) <= tol_rate * 10, (what, rel_inf(g["p"], o["p"]))
+    if ow["pw"].size:
+        assert rel_inf(g["pw"], ow["pw"]) <= tol_rate * 10, (what, rel_inf(g["pw"], ow["pw"]))
+
+
+# ------------------------------------------------------------ neighbour data
+@pytest.mark.parametrize("case", ["random", "on_boundaries", "ragged_empty"])
+def test_bin_sort_bit_exact(case):
+    import torch
+    rng = np.random.default_rng(7)
+    h = 0.013
+    cs = 2 * h
+    if case == "random":
+        x = rng.uniform(0, 1, (20011, 3)) * [0.5, 0.3, 0.2]
+    elif case == "on_boundaries":
+        k = rng.integers(0, 9, (5003, 3)).astype(np.float64)
+        x = k * cs + np.where(rng.uniform(size=(5003, 3)) < 0.5, 0.0, rng.uniform(0, cs, (5003, 3)))
+    else:
+        x = rng.uniform(0, 1, (1, 3)) * 0.1
+    lo = np.zeros(3)
+    hi = x.max(0) + 2 * cs
+    sc = S.Scene(name="pts", dp=0.01, h=h, c0=10.0, g=(0, 0, 0), lo=tuple(lo), hi=tuple(hi),
+                 phases=[S.Phase(eos="linear")], fluid_pos=x, fluid_vel=np.zeros_like(x),
+                 fluid_phase=np.zeros(len(x), np.int32), wall_pos=np.zeros((0, 3)), reinit_every=0)
+    ref = oracle.OracleSim(sc, rho=np.full(len(x), 1000.0)).cells()
+    dims = ref["dims"]
+    n_cells = int(np.prod(dims))
+    dev = torch.device("cuda")
+    xd = torch.tensor(x, dtype=torch.float64, device=dev)
+    key = torch.empty(len(x), dtype=torch.int32, device=dev)
+    order = torch.empty(len(x), dtype=torch.int32, device=dev)
+    start = torch.empty(n_cells + 1, dtype=torch.int32, device=dev)
+    st = sph.sph_bin_sort(xd.data_ptr(), len(x), lo, h, dims, key.data_ptr(), order.data_ptr(),
+                          start.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert st == sph.SPH_OK
+    assert np.array_equal(key.cpu().numpy().view(np.uint32), ref["key_f"])
+    assert np.array_equal(order.cpu().numpy(), ref["order_f"].astype(np.int32))
+    assert np.array_equal(start.cpu().numpy(), ref["start_f"].astype(np.int32))
+
+
+# ------------------------------------------------------------- create time
+@pytest.mark.parametrize("make", [lambda: S.still_water_tank(n_fluid=(10, 10, 10), wall_height=0.15),
+                                  lambda: small_dam(),
+                                  lambda: S.two_phase_still_tank()],
+                         ids=["still_tank", "dam_break", "two_phase"])
+def test_create_parity(make):
+    sc = make()
+    ref = oracle.OracleSim(sc)
+    with sph.Simulation(sc) as sim:
+        check_cells(sim, ref)
+        g = sim.state()
+    o, ow = ref.fluid(), ref.wall()
+    assert np.abs(g["normal"] - ow["normal"]).max() < 1e-6
+    assert np.array_equal(np.all(g["normal"] == 0, axis=1), np.all(ow["normal"] == 0, axis=1))
+    assert np.abs(g["x"] - o["x"]).max() < 1e-8
+    check_state(g, o, ow, sc.dp, what="create")
+    assert rel_inf(g["sigma"], o["sigma"]) < 1e-5
+    assert np.allclose(g["rhow"], ow["rhow"], rtol=1e-5)
+
+
+def test_create_parity_full_size_dam_break():
+    """80,400 fluid + 120,234 wall particles (the benchmark's dam break)."""
+    sc = S.dam_break()
+    ref = oracle.OracleSim(sc)
+    with sph.Simulation(sc) as sim:
+        check_cells(sim, ref)
+        g = sim.state()
+        sim.step(5, dt=1e-4)
+        g5 = sim.state()
+    check_state(g, ref.fluid(), ref.wall(), sc.dp, what="create")
+    ref.step(5, dt=1e-4)
+    check_state(g5, ref.fluid(), ref.wall(), sc.dp, what="5 steps")
+
+
+# --------------------------------------------------------------- stepping
+@pytest.mark.parametrize("make", [lambda: S.still_water_tank(n_fluid=(10, 10, 10), wall_height=0.15),
+                                  lambda: small_dam(),
+                                  lambda: small_dam(mu=0.5),
+                                  lambda: S.two_phase_still_tank()],
+                         ids=["still_tank", "dam_break", "dam_break_viscous", "two_phase"])
+def test_steps_parity(make):
+    sc = make()
+    ref = oracle.OracleSim(sc)
+    with sph.Simulation(sc) as sim:
+        for k, n in enumerate((1, 4, 15)):
+            dt = sim.step(n)
+            dref = ref.step(n)
+            assert abs(dt - dref) <= 1e-6 * dref
+            g = sim.state()
+            check_state(g, ref.fluid(), ref.wall(), sc.dp, what=f"after {n} more steps")
+
+
+def test_still_water_8k_fp32_100_steps():
+    """The 20^3 still-water tank for 100 CFL steps: trajectories within 1e-3 dp."""
+    sc = S.still_water_tank()
+    ref = oracle.OracleSim(sc)
+    with sph.Simulation(sc) as sim:
+        sim.step(100)
+        g = sim.state()
+        d = sim.diagnostics()
+    ref.step(100)
+    o = ref.fluid()
+    assert np.abs(g["x"] - o["x"]).max() <= TOL_X * sc.dp
+    assert np.abs(g["v"] - o["v"]).max() <= 1e-3 * max(np.abs(o["v"]).max(), 1e-3)
+    dref = ref.diagnostics()
+    assert d[0] == pytest.approx(dref[0], rel=1e-6)
+    assert d[5] == pytest.approx(dref[5], rel=1e-6)
+    assert d[7] == 0
+
+
+def test_still_water_8k_fp64_plain_100_steps():
+    """The still-water tank in the plain FP64 form agrees with the oracle to
+    FP64 round-off."""
+    sc = S.still_water_tank()
+    ref = oracle.OracleSim(sc)
+    with sph.Simulation(sc, precision=sph.SPH_FP64_PLAIN) as sim:
+        g0 = sim.state()
+        check_state(g0, ref.fluid(), ref.wall(), sc.dp, tol_rate=TOL_FP64, tol_x=1e-9, what="create")
+        sim.step(100)
+        g = sim.state()
+    ref.step(100)
+    check_state(g, ref.fluid(), ref.wall(), sc.dp, tol_rate=1e-7, tol_x=1e-7, what="100 steps")
+
+
+def test_reinit_explicit_and_periodic():
+    sc = small_dam(reinit_every=3)
+    ref = oracle.OracleSim(sc)
+    with sph.Simulation(sc) as sim:
+        sim.step(7, dt=1e-4)
+        ref.step(7, dt=1e-4)
+        sim.reinit_density()
+        ref.reinit_density()
+        g = sim.state()
+    o = ref.fluid()
+    assert rel_inf(g["rho"] - 1000.0, o["rho"] - 1000.0) < 1e-3
+    assert rel_inf(g["p"], o["p"]) < 1e-3
+
+
+def test_momentum_conserved_on_gpu():
+    """Fluid only, g = 0: sum m a vanishes to FP32 round-off (pairwise
+    antisymmetry of the momentum equation, Sec. 2.2)."""
+    sc = S.jittered_blob(n=(12, 12, 12), vel_scale=0.5, rho_jitter=0.01)
+    with sph.Simulation(sc) as sim:
+        g = sim.state()
+    a = g["a"]
+    assert np.all(np.abs(a.sum(0)) < 1e-5 * np.abs(a).sum(0))
+
+
+def test_penalty_pair_parity():
+    dp = 0.01
+    wall = np.array([[0.0, 0.0, 0.0], [0.0, 0.0, -dp]])
+    fluid = np.array([[0.0, 0.0, 0.3 * dp]])
+    sc = S.Scene(name="pen", dp=dp, h=1.3 * dp, c0=10.0, g=(0, 0, 0), lo=(-0.05, -0.05, -0.05),
+                 hi=(0.05, 0.05, 0.05), phases=[S.Phase(eos="linear", penalty=True)],
+                 fluid_pos=fluid, fluid_vel=np.zeros_like(fluid), fluid_phase=np.zeros(1, np.int32),
+                 wall_pos=wall, reinit_every=0)
+    rho = np.array([1000.5])
+    with sph.Simulation(sc, rho=rho) as sim:
+        g = sim.state()
+    o = oracle.OracleSim(sc, rho=rho).fluid()
+    assert o["a"][0, 2] > 0
+    assert rel_inf(g["a"], o["a"]) < 2e-5
+
+
+# ------------------------------------------------------------- edge cases
+def test_empty_fluid_and_no_walls():
+    sc = S.still_water_tank(n_fluid=(4, 4, 4))
+    sc.fluid_pos = np.zeros((0, 3))
+    sc.fluid_vel = np.zeros((0, 3))
+    sc.fluid_phase = np.zeros(0, np.int32)
+    with sph.Simulation(sc) as sim:
+        sim.step(2, dt=1e-4)
+        assert sim.state()["pw"].max() == 0.0
+    sc2 = S.jittered_blob(n=(5, 5, 5))
+    with sph.Simulation(sc2) as sim:
+        sim.step(2)
+        assert sim.diagnostics()[7] == 0
+
+
+def test_particle_outside_grid_is_rejected_at_create():
+    sc = small_dam()
+    sc.fluid_pos = sc.fluid_pos.copy()
+    sc.fluid_pos[5] = np.asarray(sc.hi) + 1.0
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(sc)
+    assert e.value.status == sph.SPH_ERR_DOMAIN
+
+
+def test_escaping_particle_reported_and_excluded():
+    """A lone particle (out of every other particle's support) leaves the grid
+    through x = lo: the step reports SPH_ERR_DOMAIN, the particle is excluded
+    from all interactions (a = 0) and the others match the oracle."""
+    sc = S.jittered_blob(n=(6, 6, 6), vel_scale=0.0, margin_cells=3)
+    lone = np.array([[sc.lo[0] + 0.3 * 2 * sc.h, sc.fluid_pos[:, 1].mean(), sc.fluid_pos[:, 2].mean()]])
+    sc.fluid_pos = np.concatenate([lone, sc.fluid_pos])
+    sc.fluid_vel = np.zeros_like(sc.fluid_pos)
+    sc.fluid_vel[0] = [-5.0, 0.0, 0.0]
+    sc.fluid_phase = np.zeros(sc.n_fluid, np.int32)
+    ref = oracle.OracleSim(sc)
+    with sph.Simulation(sc) as sim:
+        with pytest.raises(sph.SphError) as e:
+            for _ in range(40):
+                sim.step(1, dt=2e-4)
+                ref.step(1, dt=2e-4)
+        assert e.value.status == sph.SPH_ERR_DOMAIN
+        ref.step(1, dt=2e-4)
+        g = sim.state()
+        assert sim.diagnostics()[7] == 1
+    o = ref.fluid()
+    assert ref.diagnostics()[7] == 1
+    keep = np.arange(sc.n_fluid) != 0
+    assert np.abs(g["x"][keep] - o["x"][keep]).max() <= TOL_X * sc.dp
+    assert np.all(g["a"][0] == 0)
+
+
+def test_nonfinite_is_sticky():
+    """A density far beyond the EOS range overflows the FP32 pressure; the first
+    step reports SPH_ERR_NONFINITE and every later call SPH_ERR_STATE."""
+    sc2 = small_dam()
+    with sph.Simulation(sc2, rho=np.full(sc2.n_fluid, 1e38)) as sim:
+        with pytest.raises(sph.SphError) as e:
+            sim.step(1, dt=1e-4)
+        assert e.value.status == sph.SPH_ERR_NONFINITE
+        st, _ = sph.sph_step(sim.ctx, 1, 1e-4)
+        assert st == sph.SPH_ERR_STATE
