@@ -199,11 +199,12 @@ enum {
     SPH_K_SCAN = 2,         /* exclusive scan of cell counts (3 launches)     */
     SPH_K_SCATTER = 3,      /* first placement by arrival rank                */
     SPH_K_GATHER = 4,       /* (key, id) order, reinitialisation, EOS         */
-    SPH_K_CONTINUITY = 5,   /* Riemann continuity / summation density, EOS    */
-    SPH_K_WALL_PRESSURE = 6,/* wall dummy pressure, Eq. (wallPressure)        */
-    SPH_K_MOMENTUM = 7,     /* momentum, penalty, viscosity, gravity, kick    */
-    SPH_K_OTHER = 8,        /* create, export, diagnostics                    */
-    SPH_NK = 9
+    SPH_K_NEIGHBORS = 5,    /* per-particle neighbour lists (r < 2h)          */
+    SPH_K_CONTINUITY = 6,   /* Riemann continuity / summation density, EOS    */
+    SPH_K_WALL_PRESSURE = 7,/* wall dummy pressure, Eq. (wallPressure)        */
+    SPH_K_MOMENTUM = 8,     /* momentum, penalty, viscosity, gravity, kick    */
+    SPH_K_OTHER = 9,        /* create, export, diagnostics                    */
+    SPH_NK = 10
 };
 
 /* Per-kernel timing with CUDA events recorded on the context's stream around

@@ -41,6 +41,8 @@ struct Cfg {
     T dp, dp3, inv_dp, eta2, pen_rmin;  // dx, dx^3, 1/dx, 0.01 h^2, 1e-6 dx
     T gx, gy, gz;
     T inv_sigma0;           // 1 / (lattice number density)
+    T sigma0_hi, sigma0_lo; // lattice number density sigma^0 as an unevaluated sum
+    T inv_dp3_hi, inv_dp3_lo;  // 1/dx^3 likewise (summation-density reference)
     T cfl, body_dt;         // cfl, cfl*sqrt(h/|g|) (0 if g = 0)
     int32_t nx, ny, nz, n_cells;
     int32_t n_phases;
@@ -86,16 +88,17 @@ __device__ __forceinline__ void drift1(T& o, T& comp, T dt, T v)
 }
 
 // Move an offset back into [0, cs] and shift the cell index accordingly.
-// An offset of exactly cs (the closed upper face) keeps every pair within
-// 2h inside the 27-cell stencil, a negative one would not.
+// Offsets already in the closed interval stay where they are: an offset of
+// exactly cs (a particle on the upper face, as the FP64 binning at create
+// can leave it) still has every pair within 2h inside its 27-cell stencil,
+// while a negative offset would not.
 template <class T>
 __device__ __forceinline__ void rebin1(T& o, int32_t& c, T cs)
 {
+    if (o >= T(0) && o <= cs) return;
     T k = f_floor(o / cs);
-    if (k != T(0)) {
-        o = fma_rn(-k, cs, o);
-        c += (int32_t)k;
-    }
+    o = fma_rn(-k, cs, o);
+    c += (int32_t)k;
     if (o < T(0)) { o = add_rn(o, cs); c -= 1; }
     if (o > cs) { o = sub_rn(o, cs); c += 1; }
 }

@@ -2,7 +2,7 @@
 // normals), the FP64 state export and the FP64 diagnostics reductions.
 #pragma once
 
-#include "sph_kernels.cuh"
+#include "sph_sweeps.cuh"
 
 namespace sph {
 
@@ -16,6 +16,7 @@ struct InitCfg {
     int32_t has_rho;
     double rho0[2], z_top[2];
     int32_t eos[2];
+    double sigma0;      // lattice number density (the stored sigma is sigma - sigma0)
 };
 
 // cell of an FP64 position: c = floor((x - lo)/cs) in FP64, offset x - lo - c cs
@@ -200,7 +201,7 @@ __global__ void k_export_fluid(Cfg<T> C, InitCfg I, int32_t n, const V4<T>* __re
         o.acc[3 * i + 2] = a.z;
     }
     if (o.drho_dt) o.drho_dt[i] = a.w;
-    if (o.sigma) o.sigma[i] = sigma[k];
+    if (o.sigma) o.sigma[i] = I.sigma0 + (double)sigma[k];
 }
 
 template <class T>

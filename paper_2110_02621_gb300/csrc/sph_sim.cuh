@@ -42,6 +42,7 @@ namespace sph {
 
 inline int grid_for(int64_t n) { return (int)((n + BLOCK - 1) / BLOCK); }
 
+
 // number density of a full cubic lattice of spacing dp, self included
 inline double lattice_sigma0(double dp, double h)
 {
@@ -87,7 +88,12 @@ Cfg<T> make_cfg(const sph_params& P, const int32_t dims[3])
     C.gx = (T)P.g[0];
     C.gy = (T)P.g[1];
     C.gz = (T)P.g[2];
-    C.inv_sigma0 = (T)(1.0 / lattice_sigma0(P.dp, h));
+    const double sigma0 = lattice_sigma0(P.dp, h), inv_dp3 = 1.0 / (P.dp * P.dp * P.dp);
+    C.inv_sigma0 = (T)(1.0 / sigma0);
+    C.sigma0_hi = (T)sigma0;
+    C.sigma0_lo = (T)(sigma0 - (double)C.sigma0_hi);
+    C.inv_dp3_hi = (T)inv_dp3;
+    C.inv_dp3_lo = (T)(inv_dp3 - (double)C.inv_dp3_hi);
     C.cfl = (T)P.cfl;
     double gn = std::sqrt(P.g[0] * P.g[0] + P.g[1] * P.g[1] + P.g[2] * P.g[2]);
     C.body_dt = gn > 0.0 ? (T)(P.cfl * std::sqrt(h / gn)) : T(0);
@@ -147,6 +153,7 @@ class Sim final : public SimBase {
         I_.gamma = P.gamma_tait;
         I_.n_phases = P.n_phases;
         I_.has_rho = F.rho != nullptr;
+        I_.sigma0 = lattice_sigma0(P.dp, P.h);
         for (int k = 0; k < 2; ++k) {
             const sph_phase& ph = P.phase[k < P.n_phases ? k : 0];
             I_.rho0[k] = ph.rho0;
@@ -243,6 +250,8 @@ class Sim final : public SimBase {
         par_ = 1;
 
         // ---- wall pressure of the initial state, then a^0, sigma^0, U_max
+        s = neighbors(pos_[0], cell_[1]);
+        if (s != SPH_OK) return s;
         s = wall_pressure(vel_[1]);
         if (s != SPH_OK) return s;
         s = momentum(vel_[1], vel_[0], cell_[1], phase_[1]);  // dt = 0: writes v + 0*a
@@ -497,6 +506,9 @@ class Sim final : public SimBase {
         }
         if ((s = alloc(acc_, nf)) != SPH_OK) return s;
         if ((s = alloc(sigma_, nf)) != SPH_OK) return s;
+        if ((s = alloc(nbf_, (size_t)SUBF * LP * nf)) != SPH_OK) return s;
+        if ((s = alloc(nbw_, (size_t)SUBW * LP * nf)) != SPH_OK) return s;
+        if ((s = alloc(ncnt_, (size_t)LP * nf)) != SPH_OK) return s;
         if ((s = alloc(newcell_, nmax)) != SPH_OK) return s;
         if ((s = alloc(rank_, nmax)) != SPH_OK) return s;
         if ((s = alloc(tmp_src_, nmax)) != SPH_OK) return s;
@@ -523,25 +535,37 @@ class Sim final : public SimBase {
         return SPH_OK;
     }
 
+    // neighbour lists of the sorted fluid at positions pts (fluid) / walls
+    sph_status neighbors(const V4<T>* pts, const int4* cell)
+    {
+        if (nf_ == 0) return SPH_OK;
+        SPH_KERNEL(SPH_K_NEIGHBORS, 1,
+                   k_neighbors<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(C_, nf_, fstart_, wstart_, pts,
+                                                                                     wpos_, cell,
+                                                                       nbf_, nbw_, ncnt_));
+        return SPH_OK;
+    }
+
     // Eq. (wallPressure) from the fluid state pos[0] / vel_cur
     sph_status wall_pressure(const V4<T>* vel_cur)
     {
         if (nw_ == 0) return SPH_OK;
         SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
-                   k_wall_pressure<T><<<grid_for(nw_), BLOCK, 0, stream>>>(C_, nw_, fstart_, wpos_, wcell_, pos_[0],
+                   k_wall_pressure<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(C_, nw_, fstart_, wpos_,
+                                                                                         wcell_, pos_[0],
                                                                            vel_cur, wrho_, d_active_));
         return SPH_OK;
     }
 
     // momentum from pos[0] / vel_cur; writes acc, vel_out (final kick),
-    // sigma and U_max
+    // sigma - sigma^0 and U_max
     sph_status momentum(const V4<T>* vel_cur, V4<T>* vel_out, const int4* cell, const int32_t* phase)
     {
         if (nf_ == 0) return SPH_OK;
         SPH_KERNEL(SPH_K_MOMENTUM, 1,
-                   k_momentum<T><<<grid_for(nf_), BLOCK, 0, stream>>>(C_, nf_, fstart_, wstart_, pos_[0], vel_cur,
-                                                                      cell, phase, wpos_, wrho_, wnrm_, d_dt_, acc_,
-                                                                      vel_out, sigma_, d_vmax_, d_flags_));
+                   k_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                       C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_cur, cell, phase, wpos_, wrho_, wnrm_,
+                       d_dt_, acc_, vel_out, sigma_, d_vmax_, d_flags_));
         return SPH_OK;
     }
 
@@ -571,10 +595,12 @@ class Sim final : public SimBase {
                            C_, nf_, fstart_, tmp_src_, tmp_id_, newcell_, d_dt_, reinit ? 1 : 0, pos_[0], vel_[p],
                            drho_[0], acc_, comp_[p], sigma_, cell_[p], phase_[p], pos_[1], vel_[q], drho_[1],
                            comp_[q], cell_[q], id_[q], phase_[q]));
+            sph_status sn = neighbors(pos_[1], cell_[q]);
+            if (sn != SPH_OK) return sn;
             SPH_KERNEL(SPH_K_CONTINUITY, 1,
-                       k_continuity<T><<<grid_for(nf_), BLOCK, 0, stream>>>(
-                           C_, nf_, fstart_, wstart_, pos_[1], vel_[q], drho_[1], cell_[q], phase_[q], wpos_,
-                           wrho_, d_dt_, pos_[0], vel_[p], drho_[0], acc_));
+                       k_continuity<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                           C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[1], vel_[q], drho_[1], cell_[q],
+                           phase_[q], wpos_, wrho_, d_dt_, pos_[0], vel_[p], drho_[0], acc_, sigma_));
         }
         sph_status s = wall_pressure(vel_[p]);
         if (s != SPH_OK) return s;
@@ -626,7 +652,8 @@ class Sim final : public SimBase {
     int32_t* id_[2] = {nullptr, nullptr};
     int32_t* phase_[2] = {nullptr, nullptr};
     V4<T>* acc_ = nullptr;
-    T* sigma_ = nullptr;
+    T* sigma_ = nullptr;  // sigma - sigma^0
+    int32_t *nbf_ = nullptr, *nbw_ = nullptr, *ncnt_ = nullptr;
     int4* newcell_ = nullptr;
     int32_t *rank_ = nullptr, *tmp_src_ = nullptr, *tmp_id_ = nullptr;
     int32_t *counts_ = nullptr, *fstart_ = nullptr, *wstart_ = nullptr, *sums_ = nullptr;

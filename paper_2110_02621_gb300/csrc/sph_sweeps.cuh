@@ -1,0 +1,468 @@
+// Pair sweeps of the step (Sec. 3, compartments a-c) over per-particle
+// neighbour lists, with LP consecutive lanes per target particle.
+//
+// k_neighbors builds, once per step (after the re-binning, at the positions
+// r^{n+1} that continuity and momentum share), each fluid particle's lists of
+// fluid and wall neighbours with 0 < |r_ij| < 2h.  The LP lanes of a particle
+// split its candidates (lane l takes every LP-th particle of each of the 9
+// rows of 3 x-consecutive cells, which are contiguous in the sorted arrays)
+// and each keeps its own sub-list.  Neighbouring lane groups are consecutive
+// sorted particles, mostly of the same cell, so their candidate loads are
+// shared.  An entry is (j << 5) | code with code = (dx+1) + 3(dy+1) + 9(dz+1)
+// the cell shift of j relative to i, so r_ij = o_i - o_j - d cs is rebuilt
+// exactly from the cell-relative offsets.  Sub-lists are stored with entry k
+// of lane t = LP i + l at k * (LP n) + t, i.e. coalesced.
+//
+// The continuity and momentum kernels run the same lane groups over the
+// sub-lists and combine the LP partial sums with a fixed xor-shuffle tree
+// (deterministic).  A lane whose sub-list overflowed walks its share of the
+// 27 cells directly instead.
+#pragma once
+
+#include "sph_kernels.cuh"
+
+namespace sph {
+
+constexpr int LP = 4;        // lanes per target particle
+constexpr int SUBF = 40;     // fluid entries per lane sub-list (about 80/LP used)
+constexpr int SUBW = 16;     // wall entries per lane sub-list
+constexpr int LBLOCK = 128;  // threads per block
+
+__device__ __forceinline__ int code_of(int dx, int dy, int dz) { return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1); }
+
+template <class T>
+__device__ __forceinline__ void shift_of(const Cfg<T>& C, int code, T& sx, T& sy, T& sz)
+{
+    const int dx = code % 3 - 1, dy = (code / 3) % 3 - 1, dz = code / 9 - 1;
+    sx = T(dx) * C.cs;
+    sy = T(dy) * C.cs;
+    sz = T(dz) * C.cs;
+}
+
+// Kahan-compensated accumulation; the sum is s - c.  Used for number
+// densities, whose deviation from the lattice value is the signal.
+template <class T>
+__device__ __forceinline__ void kahan_add(T& s, T& c, T x)
+{
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// (s - c) - (ref_hi + ref_lo) without cancellation: s - ref_hi is exact for
+// s within a factor 2 of ref_hi (Sterbenz).
+template <class T>
+__device__ __forceinline__ T minus_ref(T s, T c, T ref_hi, T ref_lo)
+{
+    return (s - ref_hi) - (c + ref_lo);
+}
+
+// The LP lanes of a particle always take the same path (everything they
+// branch on is per particle), while different groups of a warp may not: the
+// group shuffles therefore name only the group's own lanes.
+__device__ __forceinline__ unsigned group_mask()
+{
+    return ((1u << LP) - 1u) << ((threadIdx.x & 31) & ~(LP - 1));
+}
+
+// sum over the LP lanes of a group (fixed tree: deterministic)
+template <class T>
+__device__ __forceinline__ T group_sum(T v)
+{
+    const unsigned m = group_mask();
+    for (int o = LP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o, LP);
+    return v;
+}
+
+// merge the compensated sums (s - c) of the LP lanes (TwoSum of the s parts)
+template <class T>
+__device__ __forceinline__ void group_kahan(T& s, T& c)
+{
+    const unsigned m = group_mask();
+    for (int o = LP / 2; o > 0; o >>= 1) {
+        const T s2 = __shfl_xor_sync(m, s, o, LP);
+        const T c2 = __shfl_xor_sync(m, c, o, LP);
+        const T t = s + s2;
+        const T bp = t - s;
+        const T err = (s - (t - bp)) + (s2 - bp);  // s + s2 = t + err exactly
+        s = t;
+        c = (c + c2) - err;
+    }
+}
+
+// Walks lane l's share (every LP-th candidate) of the 27 cells around cell c
+// of a sorted set, calling fn(j, dx, dy, dz).
+template <class T, class Fn>
+__device__ __forceinline__ void walk_share(const Cfg<T>& C, const int4& c, const int32_t* __restrict__ start, int l,
+                                           Fn&& fn)
+{
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int z = c.z + dz;
+        if (z < 0 || z >= C.nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int y = c.y + dy;
+            if (y < 0 || y >= C.ny) continue;
+            const int row = (z * C.ny + y) * C.nx;
+            const int xa = c.x > 0 ? c.x - 1 : 0;
+            const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
+            const int b = __ldg(start + row + xa), e = __ldg(start + row + xb + 1);
+            const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
+#pragma unroll 2
+            for (int j = b + l; j < e; j += LP) fn(j, j < b1 ? -1 : (j < b2 ? 0 : 1), dy, dz);
+        }
+    }
+}
+
+// --------------------------------------------------------- neighbour lists
+template <class T>
+__global__ void __launch_bounds__(LBLOCK) k_neighbors(
+    Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
+    const V4<T>* __restrict__ pos, const V4<T>* __restrict__ wpos, const int4* __restrict__ cell,
+    int32_t* __restrict__ nbf, int32_t* __restrict__ nbw, int32_t* __restrict__ cnt)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / LP, l = t % LP;
+    if (i >= n) return;
+    const int4 c = cell[i];
+    const size_t stride = (size_t)n * LP;
+    int nf = 0, nw = 0;
+    if (c.w >= 0) {
+        const V4<T> pi = pos[i];
+        walk_share(C, c, fstart, l, [&](int j, int dx, int dy, int dz) {
+            const V4<T> pj = pos[j];
+            const T rx = pi.x - pj.x - T(dx) * C.cs, ry = pi.y - pj.y - T(dy) * C.cs,
+                    rz = pi.z - pj.z - T(dz) * C.cs;
+            const T r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 < C.rc2 && r2 > T(0)) {
+                if (nf < SUBF) nbf[nf * stride + t] = (j << 5) | code_of(dx, dy, dz);
+                ++nf;
+            }
+        });
+        walk_share(C, c, wstart, l, [&](int w, int dx, int dy, int dz) {
+            const V4<T> pw = wpos[w];
+            const T rx = pi.x - pw.x - T(dx) * C.cs, ry = pi.y - pw.y - T(dy) * C.cs,
+                    rz = pi.z - pw.z - T(dz) * C.cs;
+            const T r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 < C.rc2 && r2 > T(0)) {
+                if (nw < SUBW) nbw[nw * stride + t] = (w << 5) | code_of(dx, dy, dz);
+                ++nw;
+            }
+        });
+    }
+    cnt[t] = nf | (nw << 16);
+}
+
+// Visits lane l's neighbours of particle i: from its sub-lists, or, for an
+// over-full sub-list, by walking its share of the 27 cells.
+// ff(j, p_j, rx, ry, rz, r2) for fluid, fw(w, p_w, rx, ry, rz, r2) for walls.
+template <class T, class FF, class FW>
+__device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t, const V4<T>& pi, const int4& c,
+                                              const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw,
+                                              int32_t count, const int32_t* __restrict__ fstart,
+                                              const int32_t* __restrict__ wstart, const V4<T>* __restrict__ pos,
+                                              const V4<T>* __restrict__ wpos, FF&& ff, FW&& fw)
+{
+    const int nf = count & 0xffff, nw = count >> 16;
+    const size_t stride = (size_t)n * LP;
+    auto pair = [&](const V4<T>* pts, int j, T sx, T sy, T sz, auto&& f) {
+        const V4<T> pj = pts[j];
+        const T rx = pi.x - pj.x - sx, ry = pi.y - pj.y - sy, rz = pi.z - pj.z - sz;
+        const T r2 = rx * rx + ry * ry + rz * rz;
+        return f(j, pj, rx, ry, rz, r2);
+    };
+    if (nf <= SUBF) {
+        for (int k = 0; k < nf; ++k) {
+            const int e = __ldg(nbf + k * stride + t);
+            T sx, sy, sz;
+            shift_of(C, e & 31, sx, sy, sz);
+            pair(pos, e >> 5, sx, sy, sz, ff);
+        }
+    } else {
+        walk_share(C, c, fstart, t % LP, [&](int j, int dx, int dy, int dz) {
+            const V4<T> pj = pos[j];
+            const T rx = pi.x - pj.x - T(dx) * C.cs, ry = pi.y - pj.y - T(dy) * C.cs,
+                    rz = pi.z - pj.z - T(dz) * C.cs;
+            const T r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 < C.rc2 && r2 > T(0)) ff(j, pj, rx, ry, rz, r2);
+        });
+    }
+    if (nw <= SUBW) {
+        for (int k = 0; k < nw; ++k) {
+            const int e = __ldg(nbw + k * stride + t);
+            T sx, sy, sz;
+            shift_of(C, e & 31, sx, sy, sz);
+            pair(wpos, e >> 5, sx, sy, sz, fw);
+        }
+    } else {
+        walk_share(C, c, wstart, t % LP, [&](int w, int dx, int dy, int dz) {
+            const V4<T> pw = wpos[w];
+            const T rx = pi.x - pw.x - T(dx) * C.cs, ry = pi.y - pw.y - T(dy) * C.cs,
+                    rz = pi.z - pw.z - T(dz) * C.cs;
+            const T r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 < C.rc2 && r2 > T(0)) fw(w, pw, rx, ry, rz, r2);
+        });
+    }
+}
+
+// ------------------------------------------------------------- continuity
+// Heavy (continuity) phases: Eq. (SPH_star_massConservation) with the
+// Riemann solution of Eq. (RSsolution).  Substituting v* gives, per pair,
+//   (m_j/rho_j)(v_i - v*).grad_i W_ij
+//      = m_j F [v_ij.r_ij + (p_i - p_j) r/(c rho_j)] / (rho_i + rho_j)
+// with grad_i W_ij = F r_ij, F = (dW/dr)/r; walls enter with v_w = 0,
+// (rho_w, p_w) and m_w = m_i.  Then rho^{n+1} = rho^n + dt d rho/dt (Sec. 2.6).
+// Light (summation) phases: Eq. (densitySummation), rho = m sum_j W_ij over
+// all particles and walls, self included, evaluated as
+// rho - rho0 = rho0 dx^3 (sum_j W_ij - 1/dx^3) with a compensated sum.  The
+// EOS then gives p^{n+1}.  Particles outside the grid keep their state and
+// get a = 0 (their momentum outputs are written here: nobody reads them).
+template <class T>
+__global__ void __launch_bounds__(LBLOCK) k_continuity(
+    Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
+    const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw, const int32_t* __restrict__ cnt,
+    const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel, const T* __restrict__ drho,
+    const int4* __restrict__ cell, const int32_t* __restrict__ phase,
+    const V4<T>* __restrict__ wpos, const V2<T>* __restrict__ wrho, const T* __restrict__ d_dt,
+    V4<T>* __restrict__ pos_o, V4<T>* __restrict__ vel_o, T* __restrict__ drho_o,
+    V4<T>* __restrict__ acc_o, T* __restrict__ dsig_o)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / LP;
+    const bool lead = (t % LP) == 0;
+    if (i >= n) return;  // whole lane groups: n * LP threads are live
+    const V4<T> pi = pos[i], vi = vel[i];
+    const int4 c = cell[i];
+    T d = drho[i];
+    if (c.w < 0) {
+        if (lead) {
+            pos_o[i] = pi;
+            vel_o[i] = vi;
+            drho_o[i] = d;
+            acc_o[i] = V4<T>{T(0), T(0), T(0), T(0)};
+            dsig_o[i] = T(0);
+        }
+        return;
+    }
+    const int ph = phase[i];
+    const PhaseK<T>& P = C.ph[ph];
+    const T rho_i = vi.w, p_i = pi.w;
+    const bool multi = C.n_phases > 1;
+    T drdt = T(0);
+    if (P.density == 1) {
+        T s = lead ? C.W0 : T(0), e = T(0);
+        for_neighbors(C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
+                      [&](int, const V4<T>&, T, T, T, T r2) { kahan_add(s, e, kernel_W(C, f_sqrt(r2))); },
+                      [&](int, const V4<T>&, T, T, T, T r2) { kahan_add(s, e, kernel_W(C, f_sqrt(r2))); });
+        group_kahan(s, e);
+        d = P.rho0 * C.dp3 * minus_ref(s, e, C.inv_dp3_hi, C.inv_dp3_lo);
+    } else {
+        T s = T(0);
+        for_neighbors(
+            C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
+            [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
+                const V4<T> vj = vel[j];
+                const T r = f_sqrt(r2);
+                const T F = kernel_F(C, r);
+                const T m_j = multi ? C.ph[phase[j]].m : P.m;
+                const T rv = rx * (vi.x - vj.x) + ry * (vi.y - vj.y) + rz * (vi.z - vj.z);
+                s += m_j * F * (rv + (p_i - pj.w) * r * C.inv_c0 / vj.w) / (rho_i + vj.w);
+            },
+            [&](int w, const V4<T>& pw, T rx, T ry, T rz, T r2) {
+                const V2<T> rw = wrho[w];
+                const T rho_w = ph == 0 ? rw.x : rw.y;
+                const T r = f_sqrt(r2);
+                const T F = kernel_F(C, r);
+                const T rv = rx * vi.x + ry * vi.y + rz * vi.z;
+                s += P.m * F * (rv + (p_i - pw.w) * r * C.inv_c0 / rho_w) / (rho_i + rho_w);
+            });
+        drdt = T(2) * rho_i * group_sum(s);
+        d = d + (*d_dt) * drdt;
+    }
+    if (lead) {
+        pos_o[i] = V4<T>{pi.x, pi.y, pi.z, eos_p(P, C, d)};
+        vel_o[i] = V4<T>{vi.x, vi.y, vi.z, P.rho0 + d};
+        drho_o[i] = d;
+        acc_o[i] = V4<T>{T(0), T(0), T(0), drdt};
+    }
+}
+
+// ----------------------------------------------------------- wall pressure
+// Eq. (wallPressure) with fixed walls (a_w = 0), reading the (g - a_w) term
+// with the fluid density (dimensionally consistent form):
+//   p_w = sum_f (p_f + rho_f g.r_wf) w_wf / sum_f w_wf,  r_wf = r_w - r_f,
+// w = W (one phase) or W/rho_f (several phases, Sec. 2.3).  Walls without
+// fluid support get p_w = 0.  rho_w = rho0 + EOS^-1(p_w) per phase.  LP
+// lanes per wall particle split the fluid of its 27 cells.
+template <class T>
+__global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
+    Cfg<T> C, int32_t nw, const int32_t* __restrict__ fstart, V4<T>* __restrict__ wpos,
+    const int4* __restrict__ wcell, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel,
+    V2<T>* __restrict__ wrho, unsigned long long* active)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = t / LP;
+    int has = 0;
+    if (w < nw) {
+        const int4 c = wcell[w];
+        const V4<T> pw = wpos[w];
+        const bool multi = C.n_phases > 1;
+        T num = T(0), den = T(0);
+        if (c.w >= 0) {
+            walk_share(C, c, fstart, t % LP, [&](int j, int dx, int dy, int dz) {
+                const V4<T> pf = pos[j];
+                const T rx = pw.x - pf.x - T(dx) * C.cs, ry = pw.y - pf.y - T(dy) * C.cs,
+                        rz = pw.z - pf.z - T(dz) * C.cs;
+                const T r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 >= C.rc2 || r2 == T(0)) return;
+                const T W = kernel_W(C, f_sqrt(r2));
+                const T rho_f = vel[j].w;
+                const T om = multi ? W / rho_f : W;
+                num += (pf.w + rho_f * (C.gx * rx + C.gy * ry + C.gz * rz)) * om;
+                den += om;
+            });
+        }
+        num = group_sum(num);
+        den = group_sum(den);
+        if (t % LP == 0) {
+            const T p_w = den > T(0) ? num / den : T(0);
+            has = den > T(0);
+            reinterpret_cast<T*>(wpos + w)[3] = p_w;
+            const T r0 = C.ph[0].rho0 + eos_drho(C.ph[0], C, p_w);
+            const T r1 = multi ? C.ph[1].rho0 + eos_drho(C.ph[1], C, p_w) : r0;
+            wrho[w] = V2<T>{r0, r1};
+        }
+    }
+    const int cnt = __syncthreads_count(has);
+    if (threadIdx.x == 0 && cnt) atomicAdd(active, (unsigned long long)cnt);
+}
+
+// --------------------------------------------------------------- momentum
+// Eq. (SPH_star_momentumConservation) with p* from Eq. (RSsolution) (fluid)
+// or Eq. (RSatWall) (wall); per pair -2 m_j p*/(rho_i rho_j) F r_ij, where
+//   p*/(rho_i rho_j) = (p_i/rho_i + p_j/rho_j + beta dU)/(rho_i + rho_j),
+//   dU = U_L - U_R = -v_ij.r_ij/r, beta = min(3 max(dU, 0), c).
+// Plus gravity, the Morris viscous term, and the penalty force of
+// Eq. (SPH_penaltyMethodTerm) with delta = 2|r_iw.n_w|/dx, lambda from
+// Eq. (symbc) and dx^3 restoring its units.  Then the final kick
+// v^{n+1} = v^{n+1/2} + dt/2 a^{n+1}, the number density sigma(r^{n+1}) for
+// the next reinitialisation (own phase and walls for continuity phases,
+// everything for summation phases; stored as sigma - sigma^0 from a
+// compensated sum) and U_max for the next dt.
+template <class T>
+__global__ void __launch_bounds__(LBLOCK) k_momentum(
+    Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
+    const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw, const int32_t* __restrict__ cnt,
+    const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel, const int4* __restrict__ cell,
+    const int32_t* __restrict__ phase, const V4<T>* __restrict__ wpos, const V2<T>* __restrict__ wrho,
+    const V4<T>* __restrict__ wnrm, const T* __restrict__ d_dt, V4<T>* __restrict__ acc,
+    V4<T>* __restrict__ vel_o, T* __restrict__ dsig_o, unsigned long long* vmax_bits, int32_t* flags)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / LP;
+    const bool lead = (t % LP) == 0;
+    T speed = T(0);
+    bool bad = false;
+    if (i < n) {
+        const V4<T> pi = pos[i], vi = vel[i];
+        const int4 c = cell[i];
+        if (c.w >= 0) {  // particles outside the grid were finished by k_continuity
+            const T hdt = T(0.5) * (*d_dt);
+            const int ph = phase[i];
+            const PhaseK<T>& P = C.ph[ph];
+            const bool multi = C.n_phases > 1;
+            const bool sig_all = P.density == 1;
+            const T rho_i = vi.w, p_i = pi.w, pr_i = p_i / rho_i, mu_i = P.mu;
+            T ax = T(0), ay = T(0), az = T(0), sg = lead ? C.W0 : T(0), se = T(0);
+            for_neighbors(
+                C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
+                [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
+                    const V4<T> vj = vel[j];
+                    const T r = f_sqrt(r2);
+                    T W, F;
+                    kernel_WF(C, r, W, F);
+                    const int phj = multi ? phase[j] : 0;
+                    const PhaseK<T>& Pj = C.ph[phj];
+                    const T vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+                    const T dU = -(rx * vx + ry * vy + rz * vz) / r;
+                    const T beta = tmin(T(3) * tmax(dU, T(0)), C.c0);
+                    const T coef = (pr_i + pj.w / vj.w + beta * dU) / (rho_i + vj.w);
+                    const T k = T(-2) * Pj.m * F * coef;
+                    const T mu = mu_i + Pj.mu;
+                    if (mu > T(0)) {
+                        const T kv = Pj.m * mu * r2 * F / (rho_i * vj.w * (r2 + C.eta2));
+                        ax += kv * vx;
+                        ay += kv * vy;
+                        az += kv * vz;
+                    }
+                    ax += k * rx;
+                    ay += k * ry;
+                    az += k * rz;
+                    if (sig_all || phj == ph) kahan_add(sg, se, W);
+                },
+                [&](int w, const V4<T>& pw, T rx, T ry, T rz, T r2) {
+                    const V2<T> rw = wrho[w];
+                    const T rho_w = ph == 0 ? rw.x : rw.y;
+                    const T r = f_sqrt(r2);
+                    T W, F;
+                    kernel_WF(C, r, W, F);
+                    const T coef = (pr_i + pw.w / rho_w) / (rho_i + rho_w);
+                    const T k = T(-2) * P.m * F * coef;
+                    ax += k * rx;
+                    ay += k * ry;
+                    az += k * rz;
+                    if (mu_i > T(0)) {
+                        const T kv = P.m * (T(2) * mu_i) * r2 * F / (rho_i * rho_w * (r2 + C.eta2));
+                        ax += kv * vi.x;
+                        ay += kv * vi.y;
+                        az += kv * vi.z;
+                    }
+                    if (P.penalty && r > C.pen_rmin) {
+                        const V4<T> nw = wnrm[w];
+                        const T rn = rx * nw.x + ry * nw.y + rz * nw.z;   // r_iw . n_w
+                        const T delta = T(2) * tabs(rn) * C.inv_dp;
+                        if (delta < T(1)) {
+                            const T en = -rn / r;                         // e_iw . n_w
+                            const T lam = (T(1) - delta) * (T(1) - delta) * C.inv_dp;
+                            const T Ppen = C.gamma_p * lam * tabs(p_i * en);
+                            const T kp = T(-2) * P.m / (rho_i * rho_w) * Ppen * C.dp3 * F / r;
+                            ax += kp * nw.x;
+                            ay += kp * nw.y;
+                            az += kp * nw.z;
+                        }
+                    }
+                    kahan_add(sg, se, W);
+                });
+            ax = group_sum(ax) + C.gx;
+            ay = group_sum(ay) + C.gy;
+            az = group_sum(az) + C.gz;
+            group_kahan(sg, se);
+            const V4<T> vo{fma_rn(hdt, ax, vi.x), fma_rn(hdt, ay, vi.y), fma_rn(hdt, az, vi.z), rho_i};
+            bad = !(f_finite(ax) && f_finite(ay) && f_finite(az));
+            speed = f_sqrt(vo.x * vo.x + vo.y * vo.y + vo.z * vo.z);
+            if (lead) {
+                acc[i] = V4<T>{ax, ay, az, acc[i].w};
+                vel_o[i] = vo;
+                dsig_o[i] = minus_ref(sg, se, C.sigma0_hi, C.sigma0_lo);
+            }
+        }
+    }
+    // block maximum of |v| (non-negative: the integer order of the bits is
+    // the order of the values) and the non-finite flag, one atomic per block
+    __shared__ unsigned long long smax[LBLOCK / 32];
+    unsigned long long b = to_bits(speed);
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long q = __shfl_xor_sync(0xffffffffu, b, o);
+        b = q > b ? q : b;
+    }
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = b;
+    const int nbad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        unsigned long long m = 0;
+        for (int k = 0; k < LBLOCK / 32; ++k) m = smax[k] > m ? smax[k] : m;
+        if (m) atomicMax(vmax_bits, m);
+        if (nbad) atomicOr(flags, 1);
+    }
+}
+
+}  // namespace sph

@@ -28,8 +28,8 @@ EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_grid_info", "sph_get_cells", "sph_diagnostics", "sph_counters",
            "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_profile",
            "sph_profile_read")
-KERNEL_KINDS = ("begin_step", "predict", "scan", "scatter", "gather", "continuity",
-                "wall_pressure", "momentum", "other")
+KERNEL_KINDS = ("begin_step", "predict", "scan", "scatter", "gather", "neighbors",
+                "continuity", "wall_pressure", "momentum", "other")
 SPH_NK = len(KERNEL_KINDS)
 
 

@@ -2,9 +2,12 @@
 
 Tolerances (from the method's required accuracy):
   * cell keys, sorted order, cell ranges: bit-exact;
-  * single-step accelerations and density rates: ||gpu - ref||_inf / ||ref||_inf
-    <= 2e-5 per field (a per-particle relative error is meaningless near
-    hydrostatic balance, where a ~ 0);
+  * single-step accelerations and density rates: ||gpu - ref||_inf / scale
+    <= 2e-5 per field, scale = ||ref||_inf for d rho/dt and the density, and
+    max(||a_ref||_inf, |g|) for the acceleration: near hydrostatic balance a is
+    the small difference of the pressure force and gravity, both O(|g|), and
+    FP32 rounding of the inputs alone leaves O(1e-7 |g|) per pair term
+    (a per-particle relative error is meaningless there);
   * trajectories: |x_gpu - x_ref| <= 1e-3 dp after up to 100 steps;
   * the plain FP64 form: the same fields within 1e-9.
 """
@@ -33,9 +36,9 @@ def _lib():
     sph.lib()
 
 
-def rel_inf(g, r):
+def rel_inf(g, r, floor=0.0):
     g, r = np.asarray(g), np.asarray(r)
-    den = np.abs(r).max()
+    den = max(np.abs(r).max(), floor)
     return float(np.abs(g - r).max() / den) if den > 0 else float(np.abs(g).max())
 
 
@@ -55,9 +58,24 @@ def check_cells(sim, ref, n_in_only=False):
     assert np.array_equal(g["start_w"], o["start_w"].astype(np.int32))
 
 
-def check_state(g, o, ow, dp, tol_rate=TOL_RATE, tol_x=TOL_X, what=""):
+def light_floor(sc):
+    """FP32 floor of a summation-density (light) phase acceleration.  Its
+    density is m sum_j W_ij, so the FP32 rounding of the positions
+    (eps ~ 2^-24 relative) perturbs rho - rho0 by ~rho0 eps and the pressure
+    by c0^2 rho0 eps, whose gradient over dx gives ~c0^2 eps / dx whatever
+    rho0 is (measured: 1.1 c0^2 2^-24 / dx).  Bound with a factor 4."""
+    return 4.0 * sc.c0 ** 2 * 2.0 ** -24 / sc.dp
+
+
+def check_state(g, o, ow, dp, tol_rate=TOL_RATE, tol_x=TOL_X, what="", gnorm=9.81, light=None,
+                floor=0.0):
     assert np.abs(g["x"] - o["x"]).max() <= tol_x * dp, what
-    assert rel_inf(g["a"], o["a"]) <= tol_rate, (what, rel_inf(g["a"], o["a"]))
+    heavy = np.ones(len(o["a"]), bool) if light is None else ~light
+    ea = rel_inf(g["a"][heavy], o["a"][heavy], gnorm)
+    assert ea <= tol_rate, (what, ea)
+    if light is not None and light.any():
+        el = np.abs(g["a"][light] - o["a"][light]).max()
+        assert el <= max(tol_rate * max(np.abs(o["a"]).max(), gnorm), floor), (what, el, floor)
     assert rel_inf(g["drho_dt"], o["drho_dt"]) <= tol_rate, (what, rel_inf(g["drho_dt"], o["drho_dt"]))
     assert rel_inf(g["rho"], o["rho"]) <= tol_rate, what
     assert rel_inf(g["p"], o["p"]) <= tol_rate * 10, (what, rel_inf(g["p"], o["p"]))
@@ -116,7 +134,8 @@ def test_create_parity(make):
     assert np.abs(g["normal"] - ow["normal"]).max() < 1e-6
     assert np.array_equal(np.all(g["normal"] == 0, axis=1), np.all(ow["normal"] == 0, axis=1))
     assert np.abs(g["x"] - o["x"]).max() < 1e-8
-    check_state(g, o, ow, sc.dp, what="create")
+    light = np.array([sc.phases[p].density == "summation" for p in sc.fluid_phase])
+    check_state(g, o, ow, sc.dp, what="create", light=light, floor=light_floor(sc))
     assert rel_inf(g["sigma"], o["sigma"]) < 1e-5
     assert np.allclose(g["rhow"], ow["rhow"], rtol=1e-5)
 
@@ -142,15 +161,23 @@ def test_create_parity_full_size_dam_break():
                                   lambda: S.two_phase_still_tank()],
                          ids=["still_tank", "dam_break", "dam_break_viscous", "two_phase"])
 def test_steps_parity(make):
+    """One CFL step from identical states: every field within the single-step
+    tolerance.  Then 4 and 15 more steps: the FP32 and FP64 states drift apart
+    by rounding, so only trajectories (1e-3 dp) and densities are compared."""
     sc = make()
     ref = oracle.OracleSim(sc)
+    light = np.array([sc.phases[p].density == "summation" for p in sc.fluid_phase])
     with sph.Simulation(sc) as sim:
         for k, n in enumerate((1, 4, 15)):
             dt = sim.step(n)
             dref = ref.step(n)
             assert abs(dt - dref) <= 1e-6 * dref
-            g = sim.state()
-            check_state(g, ref.fluid(), ref.wall(), sc.dp, what=f"after {n} more steps")
+            g, o = sim.state(), ref.fluid()
+            if k == 0:
+                check_state(g, o, ref.wall(), sc.dp, what="first step", light=light, floor=light_floor(sc))
+            else:
+                assert np.abs(g["x"] - o["x"]).max() <= TOL_X * sc.dp
+                assert rel_inf(g["rho"], o["rho"]) <= 1e-5
 
 
 def test_still_water_8k_fp32_100_steps():
