@@ -44,7 +44,8 @@ typedef enum {
     SPH_ERR_DOMAIN = 4,    /* fluid particles are outside the grid [lo, hi)  */
     SPH_ERR_NONFINITE = 5, /* a non-finite acceleration appeared (sticky)    */
     SPH_ERR_STATE = 6,     /* context unusable after a sticky error          */
-    SPH_ERR_UNSUPPORTED = 7
+    SPH_ERR_UNSUPPORTED = 7,
+    SPH_ERR_CAPACITY = 8   /* input larger than a fixed-size scratch allows   */
 } sph_status;
 
 enum { SPH_EOS_LINEAR = 0, SPH_EOS_TAIT = 1 };
@@ -237,6 +238,33 @@ void sph_destroy(sph_ctx* ctx);
 sph_status sph_bin_sort(const double* pos, int64_t n, const double lo[3],
                         double h, const int32_t dims[3], uint32_t* key,
                         int32_t* order, int32_t* start, void* cuda_stream);
+
+/* The same binning as sph_bin_sort, for callers that cannot allocate device
+ * memory while they run: code whose device memory is all owned by another
+ * framework's pool, loops that must not risk an out-of-memory failure or the
+ * synchronisation an allocation can cause part-way through, and callers that
+ * must not grow the process's device footprint.  The paper has no
+ * counterpart; it is a service of this library.
+ *
+ * Arguments, layout and results are those of sph_bin_sort (device arrays,
+ * outputs identical bit for bit).  Its scratch is one fixed array of
+ * SPH_BIN_SORT_NOALLOC_SCRATCH bytes inside the library, which every GPU that
+ * loads the library keeps until the process exits; the call itself allocates
+ * and frees nothing.  The scratch needs 32 bytes per particle, 8 bytes per
+ * grid cell and 4 bytes per 4096 cells, each of its 8 parts rounded up to 256
+ * bytes (about 1 M particles with 0.2 M cells, or 0.5 M particles with 2 M
+ * cells); larger inputs are refused with SPH_ERR_CAPACITY before any work is
+ * queued.
+ * The first call on each device looks up the array's device address (with
+ * that device current), so make that first call outside any CUDA stream
+ * capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (two streams, or two host threads) race on it and must be serialised
+ * by the caller.  The parts that must start at zero are cleared by each call.
+ * Errors: SPH_ERR_ARG, SPH_ERR_CAPACITY, SPH_ERR_CUDA. */
+#define SPH_BIN_SORT_NOALLOC_SCRATCH (32u << 20)
+sph_status sph_bin_sort_noalloc(const double* pos, int64_t n, const double lo[3],
+                                double h, const int32_t dims[3], uint32_t* key,
+                                int32_t* order, int32_t* start, void* cuda_stream);
 
 #ifdef __cplusplus
 }

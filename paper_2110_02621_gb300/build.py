@@ -20,7 +20,7 @@ LIB = os.path.join(OUT_DIR, "libsph_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["sph_api.cu", "sph_sort.cu", "sim_f32.cu", "sim_f64.cu"]
+SOURCES = ["sph_api.cu", "sph_sort.cu", "sim_f32.cu", "sim_f64.cu", "sph_noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -20,14 +20,16 @@ SPH_FP32, SPH_FP64_PLAIN = 0, 1
 SPH_HOST, SPH_DEVICE = 0, 1
 STATUS_NAMES = {0: "SPH_OK", 1: "SPH_ERR_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_OOM",
                 4: "SPH_ERR_DOMAIN", 5: "SPH_ERR_NONFINITE", 6: "SPH_ERR_STATE",
-                7: "SPH_ERR_UNSUPPORTED"}
+                7: "SPH_ERR_UNSUPPORTED", 8: "SPH_ERR_CAPACITY"}
 _EOS = {"linear": 0, "tait": 1}
 _DENSITY = {"continuity": 0, "summation": 1}
 _REINIT = {"none": 0, "free_surface": 1, "internal": 2}
 EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_grid_info", "sph_get_cells", "sph_diagnostics", "sph_counters",
-           "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_profile",
-           "sph_profile_read")
+           "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_bin_sort_noalloc",
+           "sph_profile", "sph_profile_read")
+SPH_ERR_CAPACITY = 8
+SPH_BIN_SORT_NOALLOC_SCRATCH = 32 << 20
 KERNEL_KINDS = ("begin_step", "predict", "scan", "scatter", "gather", "neighbors",
                 "continuity", "wall_pressure", "momentum", "other")
 SPH_NK = len(KERNEL_KINDS)
@@ -97,6 +99,7 @@ def lib() -> C.CDLL:
         L.sph_destroy.argtypes = [p]
         L.sph_destroy.restype = None
         L.sph_bin_sort.argtypes = [p, i64, p, d, p, p, p, p, p]
+        L.sph_bin_sort_noalloc.argtypes = [p, i64, p, d, p, p, p, p, p]
         L.sph_profile.argtypes = [p, C.c_uint32]
         L.sph_profile_read.argtypes = [p, p, p, p]
         for name in EXPORTS:
@@ -206,6 +209,15 @@ def sph_bin_sort(pos_dev: int, n: int, lo, h: float, dims, key_dev: int, order_d
     return lib().sph_bin_sort(C.c_void_p(pos_dev), int(n), lo_a, float(h), dims_a,
                               C.c_void_p(key_dev), C.c_void_p(order_dev),
                               C.c_void_p(start_dev), C.c_void_p(stream))
+
+
+def sph_bin_sort_noalloc(pos_dev: int, n: int, lo, h: float, dims, key_dev: int, order_dev: int,
+                         start_dev: int, stream: int = 0):
+    lo_a = (C.c_double * 3)(*lo)
+    dims_a = (C.c_int32 * 3)(*[int(v) for v in dims])
+    return lib().sph_bin_sort_noalloc(C.c_void_p(pos_dev), int(n), lo_a, float(h), dims_a,
+                                      C.c_void_p(key_dev), C.c_void_p(order_dev),
+                                      C.c_void_p(start_dev), C.c_void_p(stream))
 
 
 def sph_profile(ctx, kind_mask: int):
