@@ -47,6 +47,7 @@ FLOPS_PAIR = {
     "continuity_ff": 36,    # Riemann continuity term
     "continuity_fw": 33,
     "wall_pressure": 24,    # extrapolation sums
+    "neighbors": 11,        # per 27-cell candidate: r (6) and |r|^2 (5)
 }
 FP32_LANES_PER_SM = 128
 N_SM = 152
@@ -91,6 +92,22 @@ def pair_counts(x_f: np.ndarray, x_w: np.ndarray, h: float):
     else:
         fw, active = 0, 0
     return int(ff), int(fw), int(active)
+
+
+def candidate_tests(sim) -> int:
+    """Distance tests of the 27-cell neighbour search: for every fluid
+    particle, the fluid and wall particles of its cell and the 26 around."""
+    c = sim.cells()
+    nx, ny, nz = (int(v) for v in c["dims"])
+    occ = np.diff(c["start_f"].astype(np.int64)).reshape(nz, ny, nx)
+    occw = np.diff(c["start_w"].astype(np.int64)).reshape(nz, ny, nx)
+    tot = np.pad(occ + occw, 1)
+    box = np.zeros_like(occ)
+    for dz in range(3):
+        for dy in range(3):
+            for dx in range(3):
+                box += tot[dz:dz + nz, dy:dy + ny, dx:dx + nx]
+    return int((box * occ).sum())
 
 
 class ClockSampler:
@@ -258,7 +275,8 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     sim = sph.Simulation(sc, precision=precision, stream=stream.cuda_stream)
-    # warm-up steps, all kernel kinds timed to find the dominant one
+    # warm-up steps with every kernel timed by CUDA events on the library's
+    # stream: the per-kernel breakdown and the dominant kernel
     sim.profile(sph.KERNEL_KINDS)
     for _ in range(args.warmup):
         flush.zero_()
@@ -268,13 +286,15 @@ def run_gpu(args):
     dominant = max(step_kinds, key=lambda k: warm[k]["ms"])
     warm_total = sum(warm[k]["ms"] for k in step_kinds)
     shares = {k: round(warm[k]["ms"] / warm_total, 4) for k in step_kinds if warm_total > 0}
+    kernel_us = {k: round(warm[k]["ms"] * 1e3 / max(args.warmup, 1), 2) for k in step_kinds}
 
     st0 = sim.state()
     ff, fw, active0 = pair_counts(st0["x"], sc.wall_pos, sc.h)
     steps0, act_steps0 = sim.counters()
     launches0 = sum(v["launches"] for v in sim.profile_read().values())
 
-    sim.profile([dominant])
+    # timed region: no per-kernel events, so each step is one graph launch
+    sim.profile([])
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -299,9 +319,18 @@ def run_gpu(args):
     steps1, act_steps1 = sim.counters()
     launches1 = sum(v["launches"] for v in prof.values())
     active_mean = (act_steps1 - act_steps0) / max(steps1 - steps0, 1)
-    dom_ms = prof[dominant]["ms"] / max(prof[dominant]["timed"], 1)
     st1 = sim.state()
     ff1, fw1, active1 = pair_counts(st1["x"], sc.wall_pos, sc.h)
+    cand_tests = candidate_tests(sim)
+    # the dominant kernel's launch duration, CUDA events around each launch,
+    # on the steps that follow the timed region (same workload, cold L2)
+    sim.profile([dominant])
+    n_prof = min(args.steps, 200)
+    for _ in range(n_prof):
+        flush.zero_()
+        sim.step(1)
+    prof2 = sim.profile_read()
+    dom_ms = prof2[dominant]["ms"] / max(prof2[dominant]["timed"], 1)
     sim.close()
 
     if pg:
@@ -321,6 +350,8 @@ def run_gpu(args):
         flops = pairs_ff * FLOPS_PAIR["continuity_ff"] + pairs_fw * FLOPS_PAIR["continuity_fw"]
     elif dominant == "wall_pressure":
         flops = pairs_fw * FLOPS_PAIR["wall_pressure"]
+    elif dominant == "neighbors":
+        flops = cand_tests * FLOPS_PAIR["neighbors"]
     else:
         flops = None
     peaks = measured_peaks()
@@ -344,7 +375,8 @@ def run_gpu(args):
                        "active_wall_mean": round(active_mean, 1), "dp": sc.dp,
                        "value_fluid_only": value_fluid, "l2": "256 MB write before every timed step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "kernel_share_warmup": shares},
+                       "kernel_share_warmup": shares, "kernel_us_per_step_warmup": kernel_us,
+                       "step_launch": "one CUDA graph per step"},
             "roofline": roofline, "gpu_launches": int(launches1 - launches0), "clocks": clk,
             "host_wall_s": wall1 - wall0}
 

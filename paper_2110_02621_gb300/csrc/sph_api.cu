@@ -52,10 +52,11 @@ sph_status validate(const sph_params* P, const sph_fluid* F, const sph_wall* W, 
     for (int d = 0; d < 3; ++d) cells *= std::ceil((P->hi[d] - P->lo[d]) / cs);
     if (cells > (double)(sph::scan_max_len() - 2) || cells > 2.0e9)
         return bad(msg, "grid has too many cells (enlarge h or shrink [lo, hi))");
-    if (F->n < 0 || F->n > 2000000000) return bad(msg, "fluid.n out of range");
+    // neighbour-list entries address 2^26 particles per set
+    if (F->n < 0 || F->n >= (1 << 26)) return bad(msg, "fluid.n must be in [0, 2^26)");
     if (F->n > 0 && !F->pos) return bad(msg, "fluid.pos must not be NULL");
     int64_t nw = W ? W->n : 0;
-    if (nw < 0 || nw > 2000000000) return bad(msg, "wall.n out of range");
+    if (nw < 0 || nw >= (1 << 26)) return bad(msg, "wall.n must be in [0, 2^26)");
     if (nw > 0 && !W->pos) return bad(msg, "wall.pos must not be NULL");
     for (int64_t i = 0; i < F->n; ++i) {
         if (!finite3(F->pos + 3 * i)) return bad(msg, "non-finite fluid position");

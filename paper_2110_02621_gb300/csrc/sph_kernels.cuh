@@ -41,10 +41,11 @@ __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
 // Also clears the per-cell counters of the coming re-binning.
 template <class T>
 __global__ void k_begin_step(Cfg<T> C, const T* __restrict__ dt_fixed, unsigned long long* vmax_bits,
-                             T* d_dt, int32_t* counts, int32_t n_counts)
+                             T* d_dt, int32_t* counts, int32_t n_counts, int32_t* d_tag)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
+        *d_tag += 1;  // new wall-support tag for this step's neighbour build
         T dt = *dt_fixed;
         if (!(dt > T(0))) {
             T umax = bits_to<T>(*vmax_bits);

@@ -126,6 +126,9 @@ class Sim final : public SimBase {
     explicit Sim(cudaStream_t st) { stream = st; }
     ~Sim() override
     {
+        for (cudaGraphExec_t& g : gexec_)
+            if (g) cudaGraphExecDestroy(g);
+        if (cap_stream_) cudaStreamDestroy(cap_stream_);
         for (void* p : allocs_) cudaFree(p);
         for (EvPair& e : ev_) {
             cudaEventDestroy(e.a);
@@ -223,6 +226,8 @@ class Sim final : public SimBase {
         SPH_CUDA(cudaMemsetAsync(d_vmax_, 0, sizeof(unsigned long long), stream));
         SPH_CUDA(cudaMemsetAsync(d_flags_, 0, sizeof(int32_t), stream));
         SPH_CUDA(cudaMemsetAsync(d_active_, 0, sizeof(unsigned long long), stream));
+        SPH_CUDA(cudaMemsetAsync(d_tag_, 0, sizeof(int32_t), stream));
+        SPH_CUDA(cudaMemsetAsync(wtag_, 0xff, sizeof(int32_t) * (size_t)(nw_ > 0 ? nw_ : 1), stream));
         par_ = 0;
         if (nf_ > 0) {
             k_init_fluid<T><<<grid_for(nf_), BLOCK, 0, stream>>>(
@@ -282,7 +287,9 @@ class Sim final : public SimBase {
                                  stream));
         for (int32_t k = 0; k < nsteps; ++k) {
             bool reinit = P_.reinit_every > 0 && (steps_ % P_.reinit_every) == 0;
-            sph_status s = one_step(reinit);
+            // the kernel sequence of a step as one CUDA graph launch, unless
+            // kernels are being timed one by one
+            sph_status s = prof_mask_ ? one_step(reinit) : graph_step(reinit);
             if (s != SPH_OK) return s;
             ++steps_;
         }
@@ -509,6 +516,8 @@ class Sim final : public SimBase {
         if ((s = alloc(nbf_, (size_t)SUBF * LP * nf)) != SPH_OK) return s;
         if ((s = alloc(nbw_, (size_t)SUBW * LP * nf)) != SPH_OK) return s;
         if ((s = alloc(ncnt_, (size_t)LP * nf)) != SPH_OK) return s;
+        if ((s = alloc(wtag_, nw)) != SPH_OK) return s;
+        if ((s = alloc(d_tag_, 1)) != SPH_OK) return s;
         if ((s = alloc(newcell_, nmax)) != SPH_OK) return s;
         if ((s = alloc(rank_, nmax)) != SPH_OK) return s;
         if ((s = alloc(tmp_src_, nmax)) != SPH_OK) return s;
@@ -535,14 +544,13 @@ class Sim final : public SimBase {
         return SPH_OK;
     }
 
-    // neighbour lists of the sorted fluid at positions pts (fluid) / walls
+    // neighbour lists of the sorted fluid at positions pts / cells cell
     sph_status neighbors(const V4<T>* pts, const int4* cell)
     {
         if (nf_ == 0) return SPH_OK;
         SPH_KERNEL(SPH_K_NEIGHBORS, 1,
-                   k_neighbors<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(C_, nf_, fstart_, wstart_, pts,
-                                                                                     wpos_, cell,
-                                                                       nbf_, nbw_, ncnt_));
+                   k_neighbors<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                       C_, nf_, fstart_, wstart_, pts, wpos_, cell, nbf_, nbw_, ncnt_, wtag_, d_tag_));
         return SPH_OK;
     }
 
@@ -553,7 +561,8 @@ class Sim final : public SimBase {
         SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
                    k_wall_pressure<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(C_, nw_, fstart_, wpos_,
                                                                                          wcell_, pos_[0],
-                                                                           vel_cur, wrho_, d_active_));
+                                                                           vel_cur, wrho_, wtag_, d_tag_,
+                                                                           d_active_));
         return SPH_OK;
     }
 
@@ -580,7 +589,7 @@ class Sim final : public SimBase {
         const int p = par_, q = par_ ^ 1;
         SPH_KERNEL(SPH_K_BEGIN_STEP, 1,
                    k_begin_step<T><<<grid_for(n_cells_ + 1), BLOCK, 0, stream>>>(C_, d_dt_fixed_, d_vmax_, d_dt_,
-                                                                                counts_, n_cells_ + 1));
+                                                                                counts_, n_cells_ + 1, d_tag_));
         if (nf_ > 0)
             SPH_KERNEL(SPH_K_PREDICT, 1,
                        k_predict<T, KAHAN><<<grid_for(nf_), BLOCK, 0, stream>>>(
@@ -607,6 +616,46 @@ class Sim final : public SimBase {
         s = momentum(vel_[p], vel_[q], cell_[q], phase_[q]);
         if (s != SPH_OK) return s;
         par_ = q;
+        return SPH_OK;
+    }
+
+    // One step through a CUDA graph of its kernel sequence.  The buffer roles
+    // alternate between steps and the reinitialisation flag changes one
+    // kernel argument, so up to four graphs exist, captured on first use on
+    // an internal stream (the caller's may be the legacy default stream,
+    // which cannot be captured) and launched on the caller's stream.
+    sph_status graph_step(bool reinit)
+    {
+        const int key = (par_ << 1) | (reinit ? 1 : 0);
+        if (!gexec_[key]) {
+            if (!cap_stream_) SPH_CUDA(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
+            cudaStream_t user = stream;
+            const int par0 = par_;
+            int64_t before[SPH_NK];
+            memcpy(before, launches_, sizeof before);
+            stream = cap_stream_;
+            cudaError_t e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal);
+            sph_status s = e == cudaSuccess ? one_step(reinit) : SPH_OK;
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap_stream_, &g) : e;
+            stream = user;
+            par_ = par0;
+            for (int k = 0; k < SPH_NK; ++k) {
+                glaunch_[key][k] = launches_[k] - before[k];
+                launches_[k] = before[k];
+            }
+            if (s != SPH_OK) {
+                if (g) cudaGraphDestroy(g);
+                return s;
+            }
+            SPH_CUDA(e2);
+            e = cudaGraphInstantiate(&gexec_[key], g, 0);
+            cudaGraphDestroy(g);
+            SPH_CUDA(e);
+        }
+        SPH_CUDA(cudaGraphLaunch(gexec_[key], stream));
+        for (int k = 0; k < SPH_NK; ++k) launches_[k] += glaunch_[key][k];
+        par_ ^= 1;
         return SPH_OK;
     }
 
@@ -653,7 +702,12 @@ class Sim final : public SimBase {
     int32_t* phase_[2] = {nullptr, nullptr};
     V4<T>* acc_ = nullptr;
     T* sigma_ = nullptr;  // sigma - sigma^0
-    int32_t *nbf_ = nullptr, *nbw_ = nullptr, *ncnt_ = nullptr;
+    int32_t *nbf_ = nullptr, *nbw_ = nullptr;  // neighbour sub-lists (fluid, wall)
+    int32_t* ncnt_ = nullptr;                  // per-lane entry counts
+    int32_t *wtag_ = nullptr, *d_tag_ = nullptr;  // wall support tags, current tag
+    cudaStream_t cap_stream_ = nullptr;
+    cudaGraphExec_t gexec_[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t glaunch_[4][SPH_NK] = {};
     int4* newcell_ = nullptr;
     int32_t *rank_ = nullptr, *tmp_src_ = nullptr, *tmp_id_ = nullptr;
     int32_t *counts_ = nullptr, *fstart_ = nullptr, *wstart_ = nullptr, *sums_ = nullptr;

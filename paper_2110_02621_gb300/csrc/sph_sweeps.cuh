@@ -3,19 +3,22 @@
 //
 // k_neighbors builds, once per step (after the re-binning, at the positions
 // r^{n+1} that continuity and momentum share), each fluid particle's lists of
-// fluid and wall neighbours with 0 < |r_ij| < 2h.  The LP lanes of a particle
-// split its candidates (lane l takes every LP-th particle of each of the 9
-// rows of 3 x-consecutive cells, which are contiguous in the sorted arrays)
-// and each keeps its own sub-list.  Neighbouring lane groups are consecutive
-// sorted particles, mostly of the same cell, so their candidate loads are
-// shared.  An entry is (j << 5) | code with code = (dx+1) + 3(dy+1) + 9(dz+1)
-// the cell shift of j relative to i, so r_ij = o_i - o_j - d cs is rebuilt
-// exactly from the cell-relative offsets.  Sub-lists are stored with entry k
-// of lane t = LP i + l at k * (LP n) + t, i.e. coalesced.
+// fluid and wall neighbours with 0 < |r_ij| < 2h.  The 27 cells around a cell
+// are 9 rows of 3 x-consecutive cells, each row one contiguous range of the
+// sorted arrays.  The LP lanes of a particle split every row (lane l takes
+// every LP-th candidate) and each keeps its own sub-list; neighbouring lane
+// groups are consecutive sorted particles, mostly of the same cell, so their
+// candidate loads are shared.  An entry is (j << 6) | (dx+1) | (dy+1) << 2 |
+// (dz+1) << 4 with (dx, dy, dz) the cell of j relative to the cell of i (so
+// j < 2^26); entry k of lane t = LP i + l is stored at k (LP n) + t
+// (coalesced).  Builder and sweeps evaluate r_ij = (o_i - d cs) - o_j and its
+// square with the same rounded operations, so they agree bit for bit on
+// which pairs are within 2h.  The build also tags every wall particle with
+// fluid support in this step (the pair test is symmetric).
 //
 // The continuity and momentum kernels run the same lane groups over the
 // sub-lists and combine the LP partial sums with a fixed xor-shuffle tree
-// (deterministic).  A lane whose sub-list overflowed walks its share of the
+// (deterministic).  A lane whose sub-list overflowed scans its share of the
 // 27 cells directly instead.
 #pragma once
 
@@ -28,15 +31,21 @@ constexpr int SUBF = 40;     // fluid entries per lane sub-list (about 80/LP use
 constexpr int SUBW = 16;     // wall entries per lane sub-list
 constexpr int LBLOCK = 128;  // threads per block
 
-__device__ __forceinline__ int code_of(int dx, int dy, int dz) { return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1); }
+__device__ __forceinline__ int code_of(int dx, int dy, int dz) { return (dx + 1) | (dy + 1) << 2 | (dz + 1) << 4; }
 
 template <class T>
-__device__ __forceinline__ void shift_of(const Cfg<T>& C, int code, T& sx, T& sy, T& sz)
+__device__ __forceinline__ void shift_of(const Cfg<T>& C, int e, T& sx, T& sy, T& sz)
 {
-    const int dx = code % 3 - 1, dy = (code / 3) % 3 - 1, dz = code / 9 - 1;
-    sx = T(dx) * C.cs;
-    sy = T(dy) * C.cs;
-    sz = T(dz) * C.cs;
+    sx = T((e & 3) - 1) * C.cs;
+    sy = T(((e >> 2) & 3) - 1) * C.cs;
+    sz = T(((e >> 4) & 3) - 1) * C.cs;
+}
+
+// |r|^2 with a fixed rounding sequence (shared by builder and sweeps)
+template <class T>
+__device__ __forceinline__ T dist2(T x, T y, T z)
+{
+    return fma_rn(z, z, fma_rn(y, y, mul_rn(x, x)));
 }
 
 // Kahan-compensated accumulation; the sum is s - c.  Used for number
@@ -91,25 +100,39 @@ __device__ __forceinline__ void group_kahan(T& s, T& c)
     }
 }
 
-// Walks lane l's share (every LP-th candidate) of the 27 cells around cell c
-// of a sorted set, calling fn(j, dx, dy, dz).
+// Lane l's share (every LP-th candidate) of the 27 cells around cell c of a
+// sorted set with cell ranges start[]: fn(j, rx, ry, rz, r2, code) for every
+// candidate with 0 < r^2 < (2h)^2, o = the target's offset, code = the
+// 6-bit cell shift of j.
 template <class T, class Fn>
-__device__ __forceinline__ void walk_share(const Cfg<T>& C, const int4& c, const int32_t* __restrict__ start, int l,
-                                           Fn&& fn)
+__device__ __forceinline__ void scan_share(const Cfg<T>& C, const int4& c, const V4<T>& o,
+                                           const int32_t* __restrict__ start, const V4<T>* __restrict__ pts,
+                                           int l, Fn&& fn)
 {
+    const int xa = c.x > 0 ? c.x - 1 : 0;
+    const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
+    const T xl = o.x + C.cs, xr = o.x - C.cs;  // o_x - dx cs for dx = -1, +1
     for (int dz = -1; dz <= 1; ++dz) {
         const int z = c.z + dz;
         if (z < 0 || z >= C.nz) continue;
+        const T zs = o.z - T(dz) * C.cs;
         for (int dy = -1; dy <= 1; ++dy) {
             const int y = c.y + dy;
             if (y < 0 || y >= C.ny) continue;
+            const T ys = o.y - T(dy) * C.cs;
             const int row = (z * C.ny + y) * C.nx;
-            const int xa = c.x > 0 ? c.x - 1 : 0;
-            const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
             const int b = __ldg(start + row + xa), e = __ldg(start + row + xb + 1);
             const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
-#pragma unroll 2
-            for (int j = b + l; j < e; j += LP) fn(j, j < b1 ? -1 : (j < b2 ? 0 : 1), dy, dz);
+            const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
+#pragma unroll 4
+            for (int j = b + l; j < e; j += LP) {
+                const V4<T> pj = pts[j];
+                const int dxc = j < b1 ? 0 : (j < b2 ? 1 : 2);  // dx + 1
+                const T rx = (dxc == 0 ? xl : (dxc == 1 ? o.x : xr)) - pj.x;
+                const T ry = ys - pj.y, rz = zs - pj.z;
+                const T r2 = dist2(rx, ry, rz);
+                if (r2 < C.rc2 && r2 > T(0)) fn(j, rx, ry, rz, r2, cyz | dxc);
+            }
         }
     }
 }
@@ -119,42 +142,37 @@ template <class T>
 __global__ void __launch_bounds__(LBLOCK) k_neighbors(
     Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
     const V4<T>* __restrict__ pos, const V4<T>* __restrict__ wpos, const int4* __restrict__ cell,
-    int32_t* __restrict__ nbf, int32_t* __restrict__ nbw, int32_t* __restrict__ cnt)
+    int32_t* __restrict__ nbf, int32_t* __restrict__ nbw, int32_t* __restrict__ cnt, int32_t* __restrict__ wtag,
+    const int32_t* __restrict__ d_tag)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / LP, l = t % LP;
     if (i >= n) return;
     const int4 c = cell[i];
-    const size_t stride = (size_t)n * LP;
     int nf = 0, nw = 0;
     if (c.w >= 0) {
-        const V4<T> pi = pos[i];
-        walk_share(C, c, fstart, l, [&](int j, int dx, int dy, int dz) {
-            const V4<T> pj = pos[j];
-            const T rx = pi.x - pj.x - T(dx) * C.cs, ry = pi.y - pj.y - T(dy) * C.cs,
-                    rz = pi.z - pj.z - T(dz) * C.cs;
-            const T r2 = rx * rx + ry * ry + rz * rz;
-            if (r2 < C.rc2 && r2 > T(0)) {
-                if (nf < SUBF) nbf[nf * stride + t] = (j << 5) | code_of(dx, dy, dz);
-                ++nf;
-            }
+        const V4<T> o = pos[i];
+        const int tag = *d_tag;
+        const size_t stride = (size_t)n * LP;
+        size_t at = t;
+        scan_share(C, c, o, fstart, pos, l, [&](int j, T, T, T, T, int code) {
+            if (nf < SUBF) nbf[at] = (j << 6) | code;
+            at += stride;
+            ++nf;
         });
-        walk_share(C, c, wstart, l, [&](int w, int dx, int dy, int dz) {
-            const V4<T> pw = wpos[w];
-            const T rx = pi.x - pw.x - T(dx) * C.cs, ry = pi.y - pw.y - T(dy) * C.cs,
-                    rz = pi.z - pw.z - T(dz) * C.cs;
-            const T r2 = rx * rx + ry * ry + rz * rz;
-            if (r2 < C.rc2 && r2 > T(0)) {
-                if (nw < SUBW) nbw[nw * stride + t] = (w << 5) | code_of(dx, dy, dz);
-                ++nw;
-            }
+        at = t;
+        scan_share(C, c, o, wstart, wpos, l, [&](int w, T, T, T, T, int code) {
+            if (nw < SUBW) nbw[at] = (w << 6) | code;
+            at += stride;
+            ++nw;
+            wtag[w] = tag;
         });
     }
     cnt[t] = nf | (nw << 16);
 }
 
-// Visits lane l's neighbours of particle i: from its sub-lists, or, for an
-// over-full sub-list, by walking its share of the 27 cells.
+// Visits lane l's neighbours of particle i: its sub-list entries, or, for an
+// over-full sub-list, its share of the 27 cells.
 // ff(j, p_j, rx, ry, rz, r2) for fluid, fw(w, p_w, rx, ry, rz, r2) for walls.
 template <class T, class FF, class FW>
 __device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t, const V4<T>& pi, const int4& c,
@@ -165,43 +183,37 @@ __device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t,
 {
     const int nf = count & 0xffff, nw = count >> 16;
     const size_t stride = (size_t)n * LP;
-    auto pair = [&](const V4<T>* pts, int j, T sx, T sy, T sz, auto&& f) {
-        const V4<T> pj = pts[j];
-        const T rx = pi.x - pj.x - sx, ry = pi.y - pj.y - sy, rz = pi.z - pj.z - sz;
-        const T r2 = rx * rx + ry * ry + rz * rz;
-        return f(j, pj, rx, ry, rz, r2);
-    };
     if (nf <= SUBF) {
-        for (int k = 0; k < nf; ++k) {
-            const int e = __ldg(nbf + k * stride + t);
+        size_t at = t;
+#pragma unroll 4
+        for (int k = 0; k < nf; ++k, at += stride) {
+            const int e = __ldg(nbf + at);
             T sx, sy, sz;
-            shift_of(C, e & 31, sx, sy, sz);
-            pair(pos, e >> 5, sx, sy, sz, ff);
+            shift_of(C, e, sx, sy, sz);
+            const int j = e >> 6;
+            const V4<T> pj = pos[j];
+            const T rx = (pi.x - sx) - pj.x, ry = (pi.y - sy) - pj.y, rz = (pi.z - sz) - pj.z;
+            ff(j, pj, rx, ry, rz, dist2(rx, ry, rz));
         }
     } else {
-        walk_share(C, c, fstart, t % LP, [&](int j, int dx, int dy, int dz) {
-            const V4<T> pj = pos[j];
-            const T rx = pi.x - pj.x - T(dx) * C.cs, ry = pi.y - pj.y - T(dy) * C.cs,
-                    rz = pi.z - pj.z - T(dz) * C.cs;
-            const T r2 = rx * rx + ry * ry + rz * rz;
-            if (r2 < C.rc2 && r2 > T(0)) ff(j, pj, rx, ry, rz, r2);
-        });
+        scan_share(C, c, pi, fstart, pos, t % LP,
+                   [&](int j, T rx, T ry, T rz, T r2, int) { ff(j, pos[j], rx, ry, rz, r2); });
     }
     if (nw <= SUBW) {
-        for (int k = 0; k < nw; ++k) {
-            const int e = __ldg(nbw + k * stride + t);
+        size_t at = t;
+#pragma unroll 2
+        for (int k = 0; k < nw; ++k, at += stride) {
+            const int e = __ldg(nbw + at);
             T sx, sy, sz;
-            shift_of(C, e & 31, sx, sy, sz);
-            pair(wpos, e >> 5, sx, sy, sz, fw);
+            shift_of(C, e, sx, sy, sz);
+            const int w = e >> 6;
+            const V4<T> pw = wpos[w];
+            const T rx = (pi.x - sx) - pw.x, ry = (pi.y - sy) - pw.y, rz = (pi.z - sz) - pw.z;
+            fw(w, pw, rx, ry, rz, dist2(rx, ry, rz));
         }
     } else {
-        walk_share(C, c, wstart, t % LP, [&](int w, int dx, int dy, int dz) {
-            const V4<T> pw = wpos[w];
-            const T rx = pi.x - pw.x - T(dx) * C.cs, ry = pi.y - pw.y - T(dy) * C.cs,
-                    rz = pi.z - pw.z - T(dz) * C.cs;
-            const T r2 = rx * rx + ry * ry + rz * rz;
-            if (r2 < C.rc2 && r2 > T(0)) fw(w, pw, rx, ry, rz, r2);
-        });
+        scan_share(C, c, pi, wstart, wpos, t % LP,
+                   [&](int w, T rx, T ry, T rz, T r2, int) { fw(w, wpos[w], rx, ry, rz, r2); });
     }
 }
 
@@ -252,29 +264,30 @@ __global__ void __launch_bounds__(LBLOCK) k_continuity(
     if (P.density == 1) {
         T s = lead ? C.W0 : T(0), e = T(0);
         for_neighbors(C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
-                      [&](int, const V4<T>&, T, T, T, T r2) { kahan_add(s, e, kernel_W(C, f_sqrt(r2))); },
-                      [&](int, const V4<T>&, T, T, T, T r2) { kahan_add(s, e, kernel_W(C, f_sqrt(r2))); });
+                      [&](int, const V4<T>&, T, T, T, T r2) { kahan_add(s, e, kernel_W(C, r2 * p_rsqrt(r2))); },
+                      [&](int, const V4<T>&, T, T, T, T r2) { kahan_add(s, e, kernel_W(C, r2 * p_rsqrt(r2))); });
         group_kahan(s, e);
         d = P.rho0 * C.dp3 * minus_ref(s, e, C.inv_dp3_hi, C.inv_dp3_lo);
     } else {
         T s = T(0);
+        const T kc = C.inv_c0;
         for_neighbors(
             C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
             [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
                 const V4<T> vj = vel[j];
-                const T r = f_sqrt(r2);
+                const T r = r2 * p_rsqrt(r2);
                 const T F = kernel_F(C, r);
                 const T m_j = multi ? C.ph[phase[j]].m : P.m;
                 const T rv = rx * (vi.x - vj.x) + ry * (vi.y - vj.y) + rz * (vi.z - vj.z);
-                s += m_j * F * (rv + (p_i - pj.w) * r * C.inv_c0 / vj.w) / (rho_i + vj.w);
+                s += m_j * F * p_div(rv + p_div((p_i - pj.w) * r * kc, vj.w), rho_i + vj.w);
             },
             [&](int w, const V4<T>& pw, T rx, T ry, T rz, T r2) {
                 const V2<T> rw = wrho[w];
                 const T rho_w = ph == 0 ? rw.x : rw.y;
-                const T r = f_sqrt(r2);
+                const T r = r2 * p_rsqrt(r2);
                 const T F = kernel_F(C, r);
                 const T rv = rx * vi.x + ry * vi.y + rz * vi.z;
-                s += P.m * F * (rv + (p_i - pw.w) * r * C.inv_c0 / rho_w) / (rho_i + rho_w);
+                s += P.m * F * p_div(rv + p_div((p_i - pw.w) * r * kc, rho_w), rho_i + rho_w);
             });
         drdt = T(2) * rho_i * group_sum(s);
         d = d + (*d_dt) * drdt;
@@ -292,38 +305,36 @@ __global__ void __launch_bounds__(LBLOCK) k_continuity(
 // with the fluid density (dimensionally consistent form):
 //   p_w = sum_f (p_f + rho_f g.r_wf) w_wf / sum_f w_wf,  r_wf = r_w - r_f,
 // w = W (one phase) or W/rho_f (several phases, Sec. 2.3).  Walls without
-// fluid support get p_w = 0.  rho_w = rho0 + EOS^-1(p_w) per phase.  LP
-// lanes per wall particle split the fluid of its 27 cells.
+// fluid support (not tagged by this step's neighbour build) get p_w = 0 and
+// rho_w = rho0 at once; the others split the fluid of their 27 cells over LP
+// lanes.  rho_w = rho0 + EOS^-1(p_w) per phase.
 template <class T>
 __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
     Cfg<T> C, int32_t nw, const int32_t* __restrict__ fstart, V4<T>* __restrict__ wpos,
     const int4* __restrict__ wcell, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel,
-    V2<T>* __restrict__ wrho, unsigned long long* active)
+    V2<T>* __restrict__ wrho, const int32_t* __restrict__ wtag, const int32_t* __restrict__ d_tag,
+    unsigned long long* active)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int w = t / LP;
     int has = 0;
     if (w < nw) {
-        const int4 c = wcell[w];
-        const V4<T> pw = wpos[w];
         const bool multi = C.n_phases > 1;
         T num = T(0), den = T(0);
-        if (c.w >= 0) {
-            walk_share(C, c, fstart, t % LP, [&](int j, int dx, int dy, int dz) {
-                const V4<T> pf = pos[j];
-                const T rx = pw.x - pf.x - T(dx) * C.cs, ry = pw.y - pf.y - T(dy) * C.cs,
-                        rz = pw.z - pf.z - T(dz) * C.cs;
-                const T r2 = rx * rx + ry * ry + rz * rz;
-                if (r2 >= C.rc2 || r2 == T(0)) return;
-                const T W = kernel_W(C, f_sqrt(r2));
+        if (wtag[w] == *d_tag) {
+            const int4 c = wcell[w];
+            const V4<T> pw = wpos[w];
+            scan_share(C, c, pw, fstart, pos, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
+                const T W = kernel_W(C, r2 * p_rsqrt(r2));
+                const T p_f = reinterpret_cast<const T*>(pos + j)[3];
                 const T rho_f = vel[j].w;
-                const T om = multi ? W / rho_f : W;
-                num += (pf.w + rho_f * (C.gx * rx + C.gy * ry + C.gz * rz)) * om;
+                const T om = multi ? p_div(W, rho_f) : W;
+                num += (p_f + rho_f * (C.gx * rx + C.gy * ry + C.gz * rz)) * om;
                 den += om;
             });
+            num = group_sum(num);
+            den = group_sum(den);
         }
-        num = group_sum(num);
-        den = group_sum(den);
         if (t % LP == 0) {
             const T p_w = den > T(0) ? num / den : T(0);
             has = den > T(0);
@@ -372,25 +383,26 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
             const PhaseK<T>& P = C.ph[ph];
             const bool multi = C.n_phases > 1;
             const bool sig_all = P.density == 1;
-            const T rho_i = vi.w, p_i = pi.w, pr_i = p_i / rho_i, mu_i = P.mu;
+            const T rho_i = vi.w, p_i = pi.w, pr_i = p_div(p_i, rho_i), mu_i = P.mu;
             T ax = T(0), ay = T(0), az = T(0), sg = lead ? C.W0 : T(0), se = T(0);
             for_neighbors(
                 C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
                 [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
                     const V4<T> vj = vel[j];
-                    const T r = f_sqrt(r2);
+                    const T rinv = p_rsqrt(r2);
+                    const T r = r2 * rinv;
                     T W, F;
                     kernel_WF(C, r, W, F);
                     const int phj = multi ? phase[j] : 0;
                     const PhaseK<T>& Pj = C.ph[phj];
                     const T vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
-                    const T dU = -(rx * vx + ry * vy + rz * vz) / r;
+                    const T dU = -(rx * vx + ry * vy + rz * vz) * rinv;
                     const T beta = tmin(T(3) * tmax(dU, T(0)), C.c0);
-                    const T coef = (pr_i + pj.w / vj.w + beta * dU) / (rho_i + vj.w);
+                    const T coef = p_div(pr_i + p_div(pj.w, vj.w) + beta * dU, rho_i + vj.w);
                     const T k = T(-2) * Pj.m * F * coef;
                     const T mu = mu_i + Pj.mu;
                     if (mu > T(0)) {
-                        const T kv = Pj.m * mu * r2 * F / (rho_i * vj.w * (r2 + C.eta2));
+                        const T kv = p_div(Pj.m * mu * r2 * F, rho_i * vj.w * (r2 + C.eta2));
                         ax += kv * vx;
                         ay += kv * vy;
                         az += kv * vz;
@@ -403,16 +415,17 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
                 [&](int w, const V4<T>& pw, T rx, T ry, T rz, T r2) {
                     const V2<T> rw = wrho[w];
                     const T rho_w = ph == 0 ? rw.x : rw.y;
-                    const T r = f_sqrt(r2);
+                    const T rinv = p_rsqrt(r2);
+                    const T r = r2 * rinv;
                     T W, F;
                     kernel_WF(C, r, W, F);
-                    const T coef = (pr_i + pw.w / rho_w) / (rho_i + rho_w);
+                    const T coef = p_div(pr_i + p_div(pw.w, rho_w), rho_i + rho_w);
                     const T k = T(-2) * P.m * F * coef;
                     ax += k * rx;
                     ay += k * ry;
                     az += k * rz;
                     if (mu_i > T(0)) {
-                        const T kv = P.m * (T(2) * mu_i) * r2 * F / (rho_i * rho_w * (r2 + C.eta2));
+                        const T kv = p_div(P.m * (T(2) * mu_i) * r2 * F, rho_i * rho_w * (r2 + C.eta2));
                         ax += kv * vi.x;
                         ay += kv * vi.y;
                         az += kv * vi.z;
@@ -422,10 +435,10 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
                         const T rn = rx * nw.x + ry * nw.y + rz * nw.z;   // r_iw . n_w
                         const T delta = T(2) * tabs(rn) * C.inv_dp;
                         if (delta < T(1)) {
-                            const T en = -rn / r;                         // e_iw . n_w
+                            const T en = -rn * rinv;                      // e_iw . n_w
                             const T lam = (T(1) - delta) * (T(1) - delta) * C.inv_dp;
                             const T Ppen = C.gamma_p * lam * tabs(p_i * en);
-                            const T kp = T(-2) * P.m / (rho_i * rho_w) * Ppen * C.dp3 * F / r;
+                            const T kp = T(-2) * p_div(P.m, rho_i * rho_w) * Ppen * C.dp3 * F * rinv;
                             ax += kp * nw.x;
                             ay += kp * nw.y;
                             az += kp * nw.z;
