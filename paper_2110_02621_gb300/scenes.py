@@ -312,6 +312,26 @@ def jittered_blob(n: Tuple[int, int, int] = (16, 16, 16), dp: float = 0.01,
     return sc
 
 
+def perturbed(sc: Scene, jitter: float = 0.3, shift: Tuple[float, float, float] = (0.0, 0.0, 0.0),
+              vel_scale: float = 0.0, mu: Optional[float] = None, seed: int = SEED_JITTER,
+              reinit_every: Optional[int] = None) -> Scene:
+    """A copy of a scene with its fluid moved by ``shift`` (in units of dp)
+    plus a uniform random jitter of +-jitter*dp per coordinate, random normal
+    velocities of scale ``vel_scale`` (m/s), and optionally another viscosity
+    or reinitialisation period.  Moving the fluid towards the walls brings
+    particles within dp/2 of the first wall layer, where the penalty force is
+    active.  Used by the adjoint checks, which need every term of the step to
+    matter."""
+    rng = np.random.default_rng(seed)
+    pos = (sc.fluid_pos + np.asarray(shift, np.float64) * sc.dp
+           + rng.uniform(-jitter, jitter, size=sc.fluid_pos.shape) * sc.dp)
+    vel = rng.normal(0.0, 1.0, size=pos.shape) * vel_scale
+    phases = [dataclasses.replace(ph, mu=ph.mu if mu is None else mu) for ph in sc.phases]
+    return dataclasses.replace(
+        sc, name=sc.name + f"_perturbed{seed}", fluid_pos=pos, fluid_vel=vel, phases=phases,
+        reinit_every=sc.reinit_every if reinit_every is None else reinit_every)
+
+
 def random_points(n: int, box: Tuple[float, float, float], seed: int,
                   dp: float = 0.01) -> np.ndarray:
     """n uniform random points in [0, box) (for neighbour-search checks)."""

@@ -1,0 +1,157 @@
+"""Pins of the FP64 reference adjoint (oracle/adjoint.py), on the CPU.
+
+The PyTorch restatement of the step is checked against the independent C
+oracle (same equations, written twice), its autograd gradients against FP64
+central differences of the same runs, and both against closed forms: a lone
+particle in free fall, and the translation invariance of a wall-free blob."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytest.importorskip("scipy")
+
+import oracle  # noqa: E402
+from oracle import adjoint as A  # noqa: E402
+from paper_2110_02621_gb300 import scenes as S  # noqa: E402
+
+DT = 1e-4
+
+
+def adjoint_scene(mu=0.05, reinit_every=2):
+    """Small dam break with the fluid pushed 0.3 dp towards the floor and the
+    x = 0 wall, jittered by +-0.3 dp, random velocities of 0.3 m/s: every term
+    of the step (limiter, viscosity, penalty, reinitialisation) is active."""
+    sc = S.dam_break(tank=(0.2, 0.1, 0.12), column=(0.08, 0.1, 0.06), dp=0.01)
+    return S.perturbed(sc, jitter=0.3, shift=(-0.3, 0.0, -0.3), vel_scale=0.3, mu=mu,
+                       reinit_every=reinit_every)
+
+
+def c_oracle(sc, rho0=None):
+    return oracle.OracleSim(sc, rho=rho0)
+
+
+def setup(sc):
+    ref = c_oracle(sc)
+    rho0 = ref.fluid()["rho"].copy()
+    normals = ref.wall()["normal"].copy()
+    return ref, rho0, normals, ref.sigma0
+
+
+def test_penalty_is_active_in_the_adjoint_scene():
+    sc = adjoint_scene()
+    ref, _, normals, _ = setup(sc)
+    x = sc.fluid_pos
+    xw = sc.wall_pos
+    hit = 0
+    for i in range(len(x)):
+        _, ws = ref.neighbors(i)
+        for w in ws:
+            rn = abs(np.dot(x[i] - xw[w], normals[w]))
+            hit += (2 * rn / sc.dp < 1.0) and np.linalg.norm(normals[w]) > 0
+    assert hit > 10
+
+
+@pytest.mark.parametrize("nsteps", [0, 1, 4])
+def test_torch_step_matches_c_oracle(nsteps):
+    sc = adjoint_scene()
+    ref, rho0, normals, sigma0 = setup(sc)
+    P = A.params_from_scene(sc, normals, sigma0)
+    t = lambda a: torch.tensor(np.asarray(a, np.float64))  # noqa: E731
+    c0, gp, mu = t(sc.c0), t(sc.gamma_p), t(sc.phases[0].mu)
+    St = A.run(t(sc.fluid_pos), t(sc.fluid_vel), t(rho0), P, c0, gp, mu, nsteps, DT)
+    ref.step(nsteps, DT)
+    o, ow = ref.fluid(), ref.wall()
+
+    def rel(a, b):
+        return np.abs(np.asarray(a) - b).max() / max(np.abs(b).max(), 1e-300)
+
+    assert rel(St["x"].numpy(), o["x"]) < 1e-13
+    assert rel(St["v"].numpy(), o["v"]) < 1e-10
+    assert rel(St["rho"].numpy(), o["rho"]) < 1e-12
+    assert rel(St["p"].numpy(), o["p"]) < 1e-9
+    assert rel(St["a"].numpy(), o["a"]) < 1e-9
+    assert rel(St["pw"].numpy(), ow["pw"]) < 1e-9
+    # sigma: the C oracle recomputes it at the end of a call
+    assert rel(St["sigma"].numpy(), o["sigma"]) < 1e-12
+
+
+def _loss(sc, rho0, normals, sigma0, seed, nsteps, x=None, v=None, r=None, c0=None, gp=None,
+          mu=None):
+    P = A.params_from_scene(sc, normals, sigma0)
+    t = lambda a: torch.tensor(np.asarray(a, np.float64))  # noqa: E731
+    S_ = A.run(t(sc.fluid_pos if x is None else x), t(sc.fluid_vel if v is None else v),
+               t(rho0 if r is None else r), P, t(sc.c0 if c0 is None else c0),
+               t(sc.gamma_p if gp is None else gp), t(sc.phases[0].mu if mu is None else mu),
+               nsteps, DT)
+    L = 0.0
+    for k in ("x", "v", "rho", "pw"):
+        if seed.get(k) is not None:
+            L += float((S_[k].numpy() * seed[k]).sum())
+    return L
+
+
+def random_seed(sc, rng, probes=None):
+    seed = {"x": rng.normal(size=(sc.n_fluid, 3)), "v": rng.normal(size=(sc.n_fluid, 3)),
+            "rho": rng.normal(size=sc.n_fluid) * 1e-3, "pw": rng.normal(size=sc.n_wall) * 1e-3}
+    return seed
+
+
+def test_autograd_matches_central_differences():
+    sc = adjoint_scene()
+    _, rho0, normals, sigma0 = setup(sc)
+    rng = np.random.default_rng(7)
+    seed = random_seed(sc, rng)
+    nsteps = 3
+    _, g, _ = A.vjp(sc, normals, sigma0, rho0, nsteps, DT, seed)
+    args = dict(sc=sc, rho0=rho0, normals=normals, sigma0=sigma0, seed=seed, nsteps=nsteps)
+    checks = []
+    # steps balance truncation against the rounding of L (|L| ~ 500); a wall
+    # whose fluid support empties makes p_w jump to 0 (no support: p_w = 0),
+    # so position steps stay far below the particle spacing
+    for name, base, eps in (("x", sc.fluid_pos, 1e-7), ("v", sc.fluid_vel, 1e-5),
+                            ("rho", rho0, 1e-2)):
+        d = rng.normal(size=np.shape(base))
+        key = {"x": "x", "v": "v", "rho": "r"}[name]
+        lp = _loss(**args, **{key: base + eps * d})
+        lm = _loss(**args, **{key: base - eps * d})
+        checks.append((name, (lp - lm) / (2 * eps), float((g[name] * d).sum())))
+    for name, key, base, eps in (("c0", "c0", sc.c0, 1e-5 * sc.c0), ("gamma_p", "gp", sc.gamma_p, 1e-3),
+                                 ("mu", "mu", sc.phases[0].mu, 1e-4)):
+        lp = _loss(**args, **{key: base + eps})
+        lm = _loss(**args, **{key: base - eps})
+        checks.append((name, (lp - lm) / (2 * eps), float(g[name])))
+    for name, fd, ad in checks:
+        assert abs(fd - ad) <= 1e-6 * max(abs(ad), 1e-8) + 1e-9, (name, fd, ad)
+    # every parameter matters in this scene
+    assert abs(float(g["gamma_p"])) > 0 and abs(float(g["mu"])) > 0 and abs(float(g["c0"])) > 0
+
+
+def test_free_fall_closed_form():
+    """One particle far from everything: x_N = x0 + v0 T + g T^2/2 exactly under
+    KDK with constant g, so dL/dx0 = s_x and dL/dv0 = s_x T + s_v."""
+    sc = S.jittered_blob(n=(1, 1, 1), jitter=0.0, vel_scale=0.0)
+    sc.g = (0.0, 0.0, -9.81)
+    sc.fluid_vel = np.array([[0.1, -0.2, 0.3]])
+    rho0 = np.array([1000.0])
+    seed = {"x": np.array([[0.3, -1.0, 2.0]]), "v": np.array([[1.5, 0.5, -0.25]])}
+    n = 5
+    final, g, _ = A.vjp(sc, np.zeros((0, 3)), 1.0, rho0, n, DT, seed)
+    T = n * DT
+    x_ref = sc.fluid_pos + sc.fluid_vel * T + 0.5 * np.array(sc.g) * T * T
+    assert np.allclose(final["x"], x_ref, rtol=0, atol=1e-15)
+    assert np.allclose(g["x"], seed["x"], rtol=1e-14)
+    assert np.allclose(g["v"], seed["x"] * T + seed["v"], rtol=1e-12)
+
+
+def test_translation_invariance_of_a_free_blob():
+    """Without walls the run commutes with a translation of all particles, so
+    the gradients with respect to x0 sum to the seed summed over particles."""
+    sc = S.jittered_blob(n=(6, 6, 6), jitter=0.05, vel_scale=0.1)
+    sc.phases[0].mu = 0.01
+    sc.reinit_every = 2
+    ref = c_oracle(sc)
+    rho0 = ref.fluid()["rho"]
+    rng = np.random.default_rng(3)
+    seed = {"x": rng.normal(size=(sc.n_fluid, 3)), "v": rng.normal(size=(sc.n_fluid, 3))}
+    _, g, _ = A.vjp(sc, np.zeros((0, 3)), ref.sigma0, rho0, 3, DT, seed)
+    assert np.allclose(g["x"].sum(axis=0), seed["x"].sum(axis=0), rtol=1e-9, atol=1e-9)
