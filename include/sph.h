@@ -44,7 +44,7 @@ typedef enum {
     SPH_ERR_DOMAIN = 4,    /* fluid particles are outside the grid [lo, hi)  */
     SPH_ERR_NONFINITE = 5, /* a non-finite acceleration appeared (sticky)    */
     SPH_ERR_STATE = 6,     /* context unusable after a sticky error          */
-    SPH_ERR_UNSUPPORTED = 7,
+    SPH_ERR_UNSUPPORTED = 7, /* the call does not cover this configuration    */
     SPH_ERR_CAPACITY = 8   /* input larger than a fixed-size scratch allows   */
 } sph_status;
 
@@ -219,6 +219,61 @@ sph_status sph_profile(sph_ctx* ctx, uint32_t kind_mask);
  * number, launches[k] = all launches of kind k since creation.  Each pointer
  * may be NULL; arrays have SPH_NK entries. */
 sph_status sph_profile_read(sph_ctx* ctx, double* ms, int64_t* timed, int64_t* launches);
+
+/* ------------------------------------------------------------ adjoint
+ * Reverse-mode differentiation of a run of kick-drift-kick steps (Sec. 2.6)
+ * through the continuity and momentum equations with the Riemann solver
+ * (Eqs. (RSsolution), (SPH_star_massConservation),
+ * (SPH_star_momentumConservation)), the wall pressure extrapolation
+ * (Eq. (wallPressure)), the wall Riemann pressure (Eq. (RSatWall)), the
+ * penalty force (Eq. (SPH_penaltyMethodTerm)), the viscosity and the
+ * density reinitialisation (Eq. (eqrhosum)), with each step's neighbour
+ * sets frozen and each step's dt a constant.  The differentiated map is
+ * (x^0, v^0, rho^0; c0, gamma_p, mu) -> state after the taped steps, where
+ * x^0, v^0, rho^0 are the fluid state given to sph_create (when
+ * sph_fluid.rho was NULL, rho^0 is the hydrostatic density, whose own
+ * dependence on c0 is not differentiated).  One phase with continuity
+ * density only (SPH_ERR_UNSUPPORTED otherwise). */
+
+/* Adjoint seed: dL/d(final state), arrays in original particle order, FP64,
+ * host or device memory as the `where` argument of sph_backward says.  Any
+ * pointer may be NULL (zero). */
+typedef struct {
+    const double* x;    /* [n_fluid*3] dL/dx of the final positions          */
+    const double* v;    /* [n_fluid*3] dL/dv of the final velocities         */
+    const double* rho;  /* [n_fluid]   dL/drho of the final densities        */
+    const double* pw;   /* [n_wall]    dL/dp_w of the last step's wall
+                           pressures (in the order sph_create received)     */
+} sph_adjoint_seed;
+
+/* Gradients of L: arrays in original particle order (FP64, caller-owned,
+ * host or device memory as `where` says, NULL = not wanted), and the
+ * parameter gradients {dL/dc0, dL/dgamma_p, dL/dmu} (host). */
+typedef struct {
+    double* x;          /* [n_fluid*3] dL/dx^0   */
+    double* v;          /* [n_fluid*3] dL/dv^0   */
+    double* rho;        /* [n_fluid]   dL/drho^0 */
+    double params[3];
+} sph_adjoint_grad;
+
+/* Advance nsteps steps like sph_step, recording a checkpoint of the state
+ * before each step (about 96 bytes per fluid and 24 per wall particle in the
+ * FP32 form, twice that in FP64) and the dt used.  Taping must start right
+ * after sph_create and continue without untaped steps in between
+ * (SPH_ERR_STATE otherwise); nsteps = 0 only records the created state.
+ * The checkpoints live until sph_destroy.  Errors: those of sph_step,
+ * SPH_ERR_UNSUPPORTED, SPH_ERR_STATE, SPH_ERR_OOM. */
+sph_status sph_tape(sph_ctx* ctx, int32_t nsteps, double dt, double* dt_out);
+
+/* Backward sweep over all taped steps, newest first: each step is recomputed
+ * from its checkpoint (bit-identical, so the neighbour lists are the
+ * forward's), then the adjoint kernels run; finally the sweeps of
+ * sph_create at r^0 are differentiated.  The context's state is restored
+ * afterwards.  The state must still be the taped run's end (SPH_ERR_STATE
+ * after untaped steps).  Synchronises the stream.  Errors: SPH_ERR_ARG,
+ * SPH_ERR_STATE, SPH_ERR_OOM, SPH_ERR_CUDA. */
+sph_status sph_backward(sph_ctx* ctx, const sph_adjoint_seed* seed, sph_adjoint_grad* grad,
+                        int32_t where);
 
 /* Message of the last error on ctx (or of the last failed sph_create when
  * ctx is NULL).  The string lives until the next call on the context. */

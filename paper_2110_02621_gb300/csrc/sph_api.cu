@@ -176,6 +176,28 @@ sph_status sph_profile_read(sph_ctx* ctx, double* ms, int64_t* timed, int64_t* l
     return s != SPH_OK ? s : ctx->sim->profile_read(ms, timed, launches);
 }
 
+sph_status sph_tape(sph_ctx* ctx, int32_t nsteps, double dt, double* dt_out)
+{
+    sph_status s = usable(ctx);
+    if (s != SPH_OK) return s;
+    if (nsteps < 0 || !std::isfinite(dt)) {
+        ctx->sim->err = "nsteps must be >= 0 and dt finite";
+        return SPH_ERR_ARG;
+    }
+    return ctx->sim->tape(nsteps, dt, dt_out);
+}
+
+sph_status sph_backward(sph_ctx* ctx, const sph_adjoint_seed* seed, sph_adjoint_grad* grad, int32_t where)
+{
+    sph_status s = usable(ctx);
+    if (s != SPH_OK) return s;
+    if (!seed || !grad || (where != SPH_HOST && where != SPH_DEVICE)) {
+        ctx->sim->err = "seed and grad must not be NULL; where must be SPH_HOST or SPH_DEVICE";
+        return SPH_ERR_ARG;
+    }
+    return ctx->sim->backward(*seed, *grad, where);
+}
+
 const char* sph_last_error(const sph_ctx* ctx)
 {
     if (!ctx || !ctx->sim) return g_create_error.c_str();

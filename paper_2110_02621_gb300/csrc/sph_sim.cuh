@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "sph_internal.h"
+#include "sph_adjoint.cuh"
 #include "sph_setup.cuh"
 
 namespace sph {
@@ -320,6 +321,165 @@ class Sim final : public SimBase {
             SPH_KERNEL(SPH_K_OTHER, 1,
                        k_reinit<T><<<grid_for(nf_), BLOCK, 0, stream>>>(C_, nf_, sigma_, cell_[par_], phase_[par_],
                                                                         pos_[0], vel_[par_], drho_[0]));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        return SPH_OK;
+    }
+
+    // ------------------------------------------------------------ adjoint
+    sph_status tape(int32_t nsteps, double dt, double* dt_out) override
+    {
+        if (P_.n_phases != 1 || P_.phase[0].density != SPH_DENSITY_CONTINUITY) {
+            err = "the adjoint covers one phase with continuity density";
+            return SPH_ERR_UNSUPPORTED;
+        }
+        if (ck_.empty()) {
+            if (steps_ != 0) {
+                err = "taping must start right after sph_create";
+                return SPH_ERR_STATE;
+            }
+            ck_.emplace_back();
+            sph_status s = save(ck_.back());
+            if (s != SPH_OK) return s;
+            tape_end_ = 0;
+        } else if (steps_ != tape_end_) {
+            err = "untaped steps were taken since the last sph_tape";
+            return SPH_ERR_STATE;
+        }
+        double last = 0.0;
+        for (int32_t k = 0; k < nsteps; ++k) {
+            // ck_[k] is the state before taped step k
+            if ((size_t)ntaped_ == ck_.size()) {
+                ck_.emplace_back();
+                sph_status s = save(ck_.back());
+                if (s != SPH_OK) return s;
+            }
+            Ckpt& c = ck_[ntaped_];
+            c.reinit = P_.reinit_every > 0 && (steps_ % P_.reinit_every) == 0;
+            sph_status s = step(1, dt, &last);
+            if (s != SPH_OK) return s;
+            c.dt = host_status_->dt;
+            ++ntaped_;
+            tape_end_ = steps_;
+        }
+        if (dt_out) *dt_out = last;
+        return SPH_OK;
+    }
+
+    sph_status backward(const sph_adjoint_seed& seed, sph_adjoint_grad& grad, int32_t where) override
+    {
+        if (ck_.empty()) {
+            err = "nothing was taped";
+            return SPH_ERR_STATE;
+        }
+        if (steps_ != tape_end_) {
+            err = "untaped steps were taken since the last sph_tape";
+            return SPH_ERR_STATE;
+        }
+        sph_status s = adj_allocate();
+        if (s != SPH_OK) return s;
+        const size_t nf = (size_t)nf_, nw = (size_t)nw_;
+        // seeds and outputs on the device (FP64, original order)
+        const double *sx = seed.x, *sv = seed.v, *srho = seed.rho, *spw = seed.pw;
+        double *ox = grad.x, *ov = grad.v, *orho = grad.rho;
+        if (where == SPH_HOST) {
+            double* b = adj_io_;
+            auto up = [&](const double*& p, size_t cnt, double* dst) -> sph_status {
+                if (!p) return SPH_OK;
+                SPH_CUDA(cudaMemcpyAsync(dst, p, sizeof(double) * cnt, cudaMemcpyHostToDevice, stream));
+                p = dst;
+                return SPH_OK;
+            };
+            if ((s = up(sx, 3 * nf, b)) != SPH_OK) return s;
+            if ((s = up(sv, 3 * nf, b + 3 * nf)) != SPH_OK) return s;
+            if ((s = up(srho, nf, b + 6 * nf)) != SPH_OK) return s;
+            if ((s = up(spw, nw, b + 7 * nf)) != SPH_OK) return s;
+            ox = grad.x ? b + 7 * nf + nw : nullptr;
+            ov = grad.v ? b + 10 * nf + nw : nullptr;
+            orho = grad.rho ? b + 13 * nf + nw : nullptr;
+        }
+        if ((s = save(snap_)) != SPH_OK) return s;
+        SPH_CUDA(cudaMemsetAsync(adj_param_, 0, 3 * sizeof(double), stream));
+        int cur = 0;  // adjoint state buffers in use
+        if (nf_ > 0)
+            SPH_KERNEL(SPH_K_OTHER, 1,
+                       k_adj_seed<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, id_[par_], sx, sv, srho, gx_[0],
+                                                                         gv_[0], ga_[0]));
+        if (nw_ > 0)
+            SPH_KERNEL(SPH_K_OTHER, 1,
+                       k_adj_seed_wall<T><<<grid_for(nw_), BLOCK, 0, stream>>>(nw_, wid_, spw, gpw_[0]));
+
+        for (int64_t k = ntaped_ - 1; k >= 0; --k) {
+            const Ckpt& c = ck_[(size_t)k];
+            if ((s = restore(c)) != SPH_OK) return s;
+            // recompute the step bit-identically (same dt, same reinit)
+            host_status_->dt_fixed = c.dt;
+            SPH_CUDA(cudaMemcpyAsync(d_dt_fixed_, &host_status_->dt_fixed, sizeof(T), cudaMemcpyHostToDevice,
+                                     stream));
+            s = prof_mask_ ? one_step(c.reinit) : graph_step(c.reinit);
+            if (s != SPH_OK) return s;
+            const int p = c.par, q = p ^ 1;
+            const int nxt = cur ^ 1;
+            const T dt = c.dt;
+            if (nf_ > 0) {
+                SPH_KERNEL(SPH_K_OTHER, 1,
+                           k_adj_inverse<<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, c.id, adj_inv_));
+                SPH_KERNEL(SPH_K_OTHER, 1,
+                           k_adj_prep<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, T(0.5) * dt, gv_[cur], ga_[cur],
+                                                                              tA_));
+            }
+            if (nw_ > 0)
+                SPH_KERNEL(SPH_K_OTHER, 1,
+                           k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
+                               C_, nw_, fstart_, wpos_, wrho_, wnrm_, wcell_, wtag_, d_tag_, pos_[0], vel_[p], tA_,
+                               gpw_[cur], wc_, adj_param_));
+            if (nf_ > 0) {
+                SPH_KERNEL(SPH_K_OTHER, 1,
+                           k_adj_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                               C_, nf_, dt, 0, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_[p], drho_[0],
+                               cell_[q], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], tX_, tV_, adj_param_));
+                SPH_KERNEL(SPH_K_OTHER, 1,
+                           k_adj_continuity<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                               C_, nf_, dt, c.reinit ? 1 : 0, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[1], vel_[p],
+                               drho_[1], cell_[q], c.wpos, c.wrho, tX_, tV_, gx_[cur], id_[q], adj_inv_, c.drho,
+                               c.sigma, gx_[nxt], gv_[nxt], ga_[nxt], adj_param_));
+            }
+            if (nw_ > 0)
+                SPH_KERNEL(SPH_K_OTHER, 1,
+                           k_adj_wall_continuity<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
+                               C_, nw_, fstart_, c.wpos, c.wrho, wcell_, wtag_, d_tag_, pos_[1], vel_[p], drho_[1],
+                               tX_, gpw_[nxt], adj_param_));
+            cur = nxt;
+        }
+
+        // the sweeps of sph_create at r^0: wall pressure, a^0, sigma^0
+        if ((s = restore(ck_[0])) != SPH_OK) return s;
+        SPH_KERNEL(SPH_K_OTHER, 1, k_bump_tag<<<1, 32, 0, stream>>>(d_tag_));
+        if ((s = neighbors(pos_[0], cell_[par_])) != SPH_OK) return s;
+        const int p0 = par_;
+        if (nf_ > 0)
+            SPH_KERNEL(SPH_K_OTHER, 1,
+                       k_adj_prep<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, T(0), gv_[cur], ga_[cur], tA_));
+        if (nw_ > 0)
+            SPH_KERNEL(SPH_K_OTHER, 1,
+                       k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
+                           C_, nw_, fstart_, wpos_, wrho_, wnrm_, wcell_, wtag_, d_tag_, pos_[0], vel_[p0], tA_,
+                           gpw_[cur], wc_, adj_param_));
+        if (nf_ > 0) {
+            SPH_KERNEL(SPH_K_OTHER, 1,
+                       k_adj_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                           C_, nf_, T(0), 1, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_[p0], drho_[0],
+                           cell_[p0], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], tX_, tV_, adj_param_));
+            SPH_KERNEL(SPH_K_OTHER, 1,
+                       k_adj_export<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, id_[p0], tX_, tV_, ox, ov, orho));
+        }
+        SPH_CUDA(cudaMemcpyAsync(grad.params, adj_param_, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
+        if ((s = restore(snap_)) != SPH_OK) return s;
+        if (where == SPH_HOST) {
+            if (grad.x) SPH_CUDA(cudaMemcpyAsync(grad.x, ox, sizeof(double) * 3 * nf, cudaMemcpyDeviceToHost, stream));
+            if (grad.v) SPH_CUDA(cudaMemcpyAsync(grad.v, ov, sizeof(double) * 3 * nf, cudaMemcpyDeviceToHost, stream));
+            if (grad.rho)
+                SPH_CUDA(cudaMemcpyAsync(grad.rho, orho, sizeof(double) * nf, cudaMemcpyDeviceToHost, stream));
+        }
         SPH_CUDA(cudaStreamSynchronize(stream));
         return SPH_OK;
     }
@@ -659,6 +819,132 @@ class Sim final : public SimBase {
         return SPH_OK;
     }
 
+    // Checkpoint of the mutable state (the buffers of the current parity).
+    struct Ckpt {
+        char* buf = nullptr;
+        V4<T>*pos = nullptr, *vel = nullptr, *acc = nullptr, *comp = nullptr, *wpos = nullptr;
+        T *drho = nullptr, *sigma = nullptr;
+        int4* cell = nullptr;
+        int32_t *id = nullptr, *phase = nullptr, *fstart = nullptr;
+        V2<T>* wrho = nullptr;
+        unsigned long long *vmax = nullptr, *active = nullptr;
+        int par = 0;
+        int64_t steps = 0;
+        T dt = T(0);
+        bool reinit = false;
+    };
+
+    sph_status save(Ckpt& c)
+    {
+        const size_t nf = (size_t)nf_, nw = (size_t)nw_;
+        if (!c.buf) {
+            size_t off = 0;
+            auto take = [&](size_t bytes) {
+                size_t at = off;
+                off += (bytes + 255) & ~(size_t)255;
+                return at;
+            };
+            const size_t o_pos = take(nf * sizeof(V4<T>)), o_vel = take(nf * sizeof(V4<T>)),
+                         o_acc = take(nf * sizeof(V4<T>)), o_comp = take(nf * sizeof(V4<T>)),
+                         o_drho = take(nf * sizeof(T)), o_sig = take(nf * sizeof(T)),
+                         o_cell = take(nf * sizeof(int4)), o_id = take(nf * sizeof(int32_t)),
+                         o_ph = take(nf * sizeof(int32_t)), o_wpos = take(nw * sizeof(V4<T>)),
+                         o_wrho = take(nw * sizeof(V2<T>)), o_vm = take(sizeof(unsigned long long)),
+                         o_ac = take(sizeof(unsigned long long)),
+                         o_fs = take(((size_t)n_cells_ + 2) * sizeof(int32_t));
+            sph_status s = alloc(c.buf, off);
+            if (s != SPH_OK) return s;
+            c.pos = (V4<T>*)(c.buf + o_pos);
+            c.vel = (V4<T>*)(c.buf + o_vel);
+            c.acc = (V4<T>*)(c.buf + o_acc);
+            c.comp = (V4<T>*)(c.buf + o_comp);
+            c.drho = (T*)(c.buf + o_drho);
+            c.sigma = (T*)(c.buf + o_sig);
+            c.cell = (int4*)(c.buf + o_cell);
+            c.id = (int32_t*)(c.buf + o_id);
+            c.phase = (int32_t*)(c.buf + o_ph);
+            c.wpos = (V4<T>*)(c.buf + o_wpos);
+            c.wrho = (V2<T>*)(c.buf + o_wrho);
+            c.vmax = (unsigned long long*)(c.buf + o_vm);
+            c.active = (unsigned long long*)(c.buf + o_ac);
+            c.fstart = (int32_t*)(c.buf + o_fs);
+        }
+        const int p = par_;
+        auto cp = [&](void* dst, const void* src, size_t bytes) -> sph_status {
+            if (bytes) SPH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream));
+            return SPH_OK;
+        };
+        sph_status s;
+        if ((s = cp(c.pos, pos_[0], nf * sizeof(V4<T>))) != SPH_OK) return s;
+        if ((s = cp(c.vel, vel_[p], nf * sizeof(V4<T>))) != SPH_OK) return s;
+        if ((s = cp(c.acc, acc_, nf * sizeof(V4<T>))) != SPH_OK) return s;
+        if ((s = cp(c.comp, comp_[p], nf * sizeof(V4<T>))) != SPH_OK) return s;
+        if ((s = cp(c.drho, drho_[0], nf * sizeof(T))) != SPH_OK) return s;
+        if ((s = cp(c.sigma, sigma_, nf * sizeof(T))) != SPH_OK) return s;
+        if ((s = cp(c.cell, cell_[p], nf * sizeof(int4))) != SPH_OK) return s;
+        if ((s = cp(c.id, id_[p], nf * sizeof(int32_t))) != SPH_OK) return s;
+        if ((s = cp(c.phase, phase_[p], nf * sizeof(int32_t))) != SPH_OK) return s;
+        if ((s = cp(c.wpos, wpos_, nw * sizeof(V4<T>))) != SPH_OK) return s;
+        if ((s = cp(c.wrho, wrho_, nw * sizeof(V2<T>))) != SPH_OK) return s;
+        if ((s = cp(c.vmax, d_vmax_, sizeof(unsigned long long))) != SPH_OK) return s;
+        if ((s = cp(c.active, d_active_, sizeof(unsigned long long))) != SPH_OK) return s;
+        // cell ranges of the saved order (recomputed by a step, but read by the
+        // create-time sweeps and by sph_get_cells)
+        if ((s = cp(c.fstart, fstart_, ((size_t)n_cells_ + 2) * sizeof(int32_t))) != SPH_OK) return s;
+        c.par = p;
+        c.steps = steps_;
+        return SPH_OK;
+    }
+
+    sph_status restore(const Ckpt& c)
+    {
+        const size_t nf = (size_t)nf_, nw = (size_t)nw_;
+        const int p = c.par;
+        auto cp = [&](void* dst, const void* src, size_t bytes) -> sph_status {
+            if (bytes) SPH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream));
+            return SPH_OK;
+        };
+        sph_status s;
+        if ((s = cp(pos_[0], c.pos, nf * sizeof(V4<T>))) != SPH_OK) return s;
+        if ((s = cp(vel_[p], c.vel, nf * sizeof(V4<T>))) != SPH_OK) return s;
+        if ((s = cp(acc_, c.acc, nf * sizeof(V4<T>))) != SPH_OK) return s;
+        if ((s = cp(comp_[p], c.comp, nf * sizeof(V4<T>))) != SPH_OK) return s;
+        if ((s = cp(drho_[0], c.drho, nf * sizeof(T))) != SPH_OK) return s;
+        if ((s = cp(sigma_, c.sigma, nf * sizeof(T))) != SPH_OK) return s;
+        if ((s = cp(cell_[p], c.cell, nf * sizeof(int4))) != SPH_OK) return s;
+        if ((s = cp(id_[p], c.id, nf * sizeof(int32_t))) != SPH_OK) return s;
+        if ((s = cp(phase_[p], c.phase, nf * sizeof(int32_t))) != SPH_OK) return s;
+        if ((s = cp(wpos_, c.wpos, nw * sizeof(V4<T>))) != SPH_OK) return s;
+        if ((s = cp(wrho_, c.wrho, nw * sizeof(V2<T>))) != SPH_OK) return s;
+        if ((s = cp(d_vmax_, c.vmax, sizeof(unsigned long long))) != SPH_OK) return s;
+        if ((s = cp(d_active_, c.active, sizeof(unsigned long long))) != SPH_OK) return s;
+        if ((s = cp(fstart_, c.fstart, ((size_t)n_cells_ + 2) * sizeof(int32_t))) != SPH_OK) return s;
+        par_ = p;
+        steps_ = c.steps;
+        return SPH_OK;
+    }
+
+    // adjoint work buffers, allocated on the first backward sweep
+    sph_status adj_allocate()
+    {
+        if (adj_param_) return SPH_OK;
+        const size_t nf = (size_t)nf_, nw = (size_t)nw_;
+        sph_status s;
+        for (int b = 0; b < 2; ++b) {
+            if ((s = alloc(gx_[b], nf)) != SPH_OK) return s;
+            if ((s = alloc(gv_[b], nf)) != SPH_OK) return s;
+            if ((s = alloc(ga_[b], nf)) != SPH_OK) return s;
+            if ((s = alloc(gpw_[b], nw)) != SPH_OK) return s;
+        }
+        if ((s = alloc(tA_, nf)) != SPH_OK) return s;
+        if ((s = alloc(tX_, nf)) != SPH_OK) return s;
+        if ((s = alloc(tV_, nf)) != SPH_OK) return s;
+        if ((s = alloc(adj_inv_, nf)) != SPH_OK) return s;
+        if ((s = alloc(wc_, nw)) != SPH_OK) return s;
+        if ((s = alloc(adj_io_, 14 * nf + nw)) != SPH_OK) return s;
+        return alloc(adj_param_, 3);
+    }
+
     sph_status prof_begin(int kind)
     {
         if (!((prof_mask_ >> kind) & 1u) || ev_used_ >= kMaxEvents) return SPH_OK;
@@ -724,6 +1010,18 @@ class Sim final : public SimBase {
     unsigned long long* d_active_ = nullptr;
     double* diag_partial_ = nullptr;
     double* diag_out_ = nullptr;
+    // adjoint: checkpoints (ck_[k] = state before taped step k), snapshot,
+    // adjoint state (x, d), (v, sigma), a, p_w in two parities, step temporaries
+    std::vector<Ckpt> ck_;
+    Ckpt snap_;
+    int64_t ntaped_ = 0, tape_end_ = -1;
+    V4<T>*gx_[2] = {nullptr, nullptr}, *gv_[2] = {nullptr, nullptr}, *ga_[2] = {nullptr, nullptr};
+    T* gpw_[2] = {nullptr, nullptr};
+    V4<T>*tA_ = nullptr, *tX_ = nullptr, *tV_ = nullptr;
+    int32_t* adj_inv_ = nullptr;
+    T* wc_ = nullptr;
+    double* adj_io_ = nullptr;
+    double* adj_param_ = nullptr;
     HostStatus* host_status_ = nullptr;
     std::vector<void*> allocs_;
     uint32_t prof_mask_ = 0;

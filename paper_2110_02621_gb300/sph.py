@@ -27,7 +27,7 @@ _REINIT = {"none": 0, "free_surface": 1, "internal": 2}
 EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_grid_info", "sph_get_cells", "sph_diagnostics", "sph_counters",
            "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_bin_sort_noalloc",
-           "sph_profile", "sph_profile_read")
+           "sph_profile", "sph_profile_read", "sph_tape", "sph_backward")
 SPH_ERR_CAPACITY = 8
 SPH_BIN_SORT_NOALLOC_SCRATCH = 32 << 20
 KERNEL_KINDS = ("begin_step", "predict", "scan", "scatter", "gather", "neighbors",
@@ -61,6 +61,15 @@ class sph_wall(C.Structure):
 class sph_state_out(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in ("pos", "vel", "rho", "p", "acc", "drho_dt",
                                           "sigma", "pw", "rhow", "normal")]
+
+
+class sph_adjoint_seed(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("x", "v", "rho", "pw")]
+
+
+class sph_adjoint_grad(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("v", C.c_void_p), ("rho", C.c_void_p),
+                ("params", C.c_double * 3)]
 
 
 class SphError(RuntimeError):
@@ -102,6 +111,8 @@ def lib() -> C.CDLL:
         L.sph_bin_sort_noalloc.argtypes = [p, i64, p, d, p, p, p, p, p]
         L.sph_profile.argtypes = [p, C.c_uint32]
         L.sph_profile_read.argtypes = [p, p, p, p]
+        L.sph_tape.argtypes = [p, i32, d, p]
+        L.sph_backward.argtypes = [p, p, p, i32]
         for name in EXPORTS:
             if name not in ("sph_last_error", "sph_destroy"):
                 getattr(L, name).restype = st
@@ -232,6 +243,16 @@ def sph_profile_read(ctx):
     return st, ms, timed, launches
 
 
+def sph_tape(ctx, nsteps: int, dt: float = 0.0):
+    last = C.c_double(0.0)
+    st = lib().sph_tape(ctx, int(nsteps), float(dt), C.byref(last))
+    return st, last.value
+
+
+def sph_backward(ctx, seed: sph_adjoint_seed, grad: sph_adjoint_grad, where: int = SPH_HOST):
+    return lib().sph_backward(ctx, C.byref(seed), C.byref(grad), int(where))
+
+
 # ------------------------------------------------------------ convenience
 class Simulation:
     """One simulation context on the current CUDA device and stream."""
@@ -329,3 +350,22 @@ class Simulation:
         _check(st, self.ctx)
         return {k: {"ms": float(ms[i]), "timed": int(timed[i]), "launches": int(launches[i])}
                 for i, k in enumerate(KERNEL_KINDS)}
+
+    def tape(self, n: int = 1, dt: float = 0.0) -> float:
+        """Advance n steps recording checkpoints for backward()."""
+        st, last = sph_tape(self.ctx, n, dt)
+        _check(st, self.ctx)
+        return last
+
+    def backward(self, seed: dict) -> dict:
+        """Gradients of L = sum(seed_x.x_N) + sum(seed_v.v_N) + sum(seed_rho rho_N)
+        + sum(seed_pw p_w,N) with respect to the created state (x0, v0, rho0)
+        and (c0, gamma_p, mu).  Host arrays in original particle order."""
+        keep = {k: None if seed.get(k) is None else np.ascontiguousarray(seed[k], np.float64)
+                for k in ("x", "v", "rho", "pw")}
+        s = sph_adjoint_seed(*(_ptr(keep[k]) for k in ("x", "v", "rho", "pw")))
+        out = {"x": np.zeros((self.nf, 3)), "v": np.zeros((self.nf, 3)), "rho": np.zeros(self.nf)}
+        g = sph_adjoint_grad(_ptr(out["x"]), _ptr(out["v"]), _ptr(out["rho"]))
+        _check(sph_backward(self.ctx, s, g, SPH_HOST), self.ctx)
+        out["c0"], out["gamma_p"], out["mu"] = (float(g.params[k]) for k in range(3))
+        return out

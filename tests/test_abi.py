@@ -45,17 +45,21 @@ int main(void) {
          sizeof(sph_wall), sizeof(sph_state_out));
   printf("%zu %zu %zu %zu\n", offsetof(sph_params, phase), offsetof(sph_params, precision),
          offsetof(sph_params, n_phases), offsetof(sph_state_out, normal));
+  printf("%zu %zu %zu\n", sizeof(sph_adjoint_seed), sizeof(sph_adjoint_grad),
+         offsetof(sph_adjoint_grad, params));
   return 0;
 }
 ''')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-std=c11", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
-    sizes, offs = subprocess.check_output([str(exe)]).decode().split("\n")[:2]
+    sizes, offs, adj = subprocess.check_output([str(exe)]).decode().split("\n")[:3]
     assert [int(v) for v in sizes.split()] == [C.sizeof(sph.sph_phase), C.sizeof(sph.sph_params),
                                                C.sizeof(sph.sph_fluid), C.sizeof(sph.sph_wall),
                                                C.sizeof(sph.sph_state_out)]
     assert [int(v) for v in offs.split()] == [sph.sph_params.phase.offset, sph.sph_params.precision.offset,
                                               sph.sph_params.n_phases.offset, sph.sph_state_out.normal.offset]
+    assert [int(v) for v in adj.split()] == [C.sizeof(sph.sph_adjoint_seed), C.sizeof(sph.sph_adjoint_grad),
+                                             sph.sph_adjoint_grad.params.offset]
 
 
 def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
