@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64-form, accuracy and adjoint measurements")
     return ap.parse_args()
 
 
@@ -282,7 +284,7 @@ def run_gpu(args):
         flush.zero_()
         sim.step(1)
     warm = sim.profile_read()
-    step_kinds = [k for k in sph.KERNEL_KINDS if k != "other"]
+    step_kinds = [k for k in sph.KERNEL_KINDS if k != "other" and not k.startswith("adj")]
     dominant = max(step_kinds, key=lambda k: warm[k]["ms"])
     warm_total = sum(warm[k]["ms"] for k in step_kinds)
     shares = {k: round(warm[k]["ms"] / warm_total, 4) for k in step_kinds if warm_total > 0}
@@ -382,6 +384,10 @@ def run_gpu(args):
 
     if rank == 0 and world == 1 and not args.no_e2e:
         line["e2e"] = e2e(sc, args.steps, precision, stream, active_mean)
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["fp64_plain"] = fp64_throughput(sc, min(args.steps, 200), stream, flush)
+        line["accuracy"] = accuracy(sc)
+        line["adjoint"] = adjoint_block(stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, active_mean, args.cpu_seconds)
     if rank == 0:
@@ -389,6 +395,142 @@ def run_gpu(args):
     if pg:
         pg.destroy_process_group()
     return 0
+
+
+def start_dt(sc) -> float:
+    """The CFL time step of a fluid at rest (Sec. 2.6), used as a fixed dt
+    where runs are compared."""
+    dt = sc.cfl * sc.h / sc.c0
+    gn = float(np.linalg.norm(sc.g))
+    return min(dt, sc.cfl * (sc.h / gn) ** 0.5) if gn > 0 else dt
+
+
+def fp64_throughput(sc, steps, stream, flush):
+    """The plain FP64 form of the same step on the same workload."""
+    import torch
+    from paper_2110_02621_gb300 import sph
+    sim = sph.Simulation(sc, precision=sph.SPH_FP64_PLAIN, stream=stream.cuda_stream)
+    for _ in range(5):
+        flush.zero_()
+        sim.step(1)
+    s0, a0 = sim.counters()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sim.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    s1, a1 = sim.counters()
+    sim.close()
+    active = (a1 - a0) / max(s1 - s0, 1)
+    return {"value": (sc.n_fluid + active) * steps / (t_ms / 1e3) / 1e6, "unit": UNIT,
+            "value_fluid_only": sc.n_fluid * steps / (t_ms / 1e3) / 1e6,
+            "ms_per_step": t_ms / steps, "steps": steps, "dtype": "f64"}
+
+
+def accuracy(sc, nsteps: int = 20):
+    """Both GPU forms against the FP64 oracle after nsteps steps of fixed dt
+    from the same initial state."""
+    import oracle
+    from paper_2110_02621_gb300 import sph
+    oracle.build()
+    dt = start_dt(sc)
+    ref = oracle.OracleSim(sc)
+    ref.step(nsteps, dt)
+    o, ow = ref.fluid(), ref.wall()
+    ref.close()
+    gnorm = float(np.linalg.norm(sc.g))
+
+    def rel(a, b, floor=0.0):
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), floor))
+
+    out = {"steps": nsteps, "dt": dt, "against": "FP64 oracle (C, host)"}
+    for name, prec in (("fp32", sph.SPH_FP32), ("fp64_plain", sph.SPH_FP64_PLAIN)):
+        s = sph.Simulation(sc, precision=prec)
+        s.step(nsteps, dt)
+        g = s.state()
+        s.close()
+        out[name] = {"x_max_err_dp": float(np.abs(g["x"] - o["x"]).max() / sc.dp),
+                     "rho_rel_err": rel(g["rho"], o["rho"]), "p_rel_err": rel(g["p"], o["p"]),
+                     "pw_rel_err": rel(g["pw"], ow["pw"]),
+                     "a_rel_err": rel(g["a"], o["a"], gnorm),
+                     "drho_dt_rel_err": rel(g["drho_dt"], o["drho_dt"])}
+    return out
+
+
+def adjoint_block(stream, reps: int = 3):
+    """Forward + backward against forward alone on the differentiable dam break
+    (dp = 0.0075: 188,680 fluid particles, 10 steps of fixed dt, loss = sum of
+    squared wall pressures of 64 probe particles behind the water column), and
+    the FP32 gradients against the plain FP64 form's."""
+    import torch
+    from paper_2110_02621_gb300 import scenes, sph
+    sc = scenes.standard("dam_break_adjoint_189k")
+    dt = start_dt(sc)
+    n = sc.steps
+    mask = np.zeros(sc.n_wall)
+    mask[sc.probes] = 1.0
+
+    def forward_ms():
+        sim = sph.Simulation(sc, precision=sph.SPH_FP32, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.step(n, dt)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        sim.close()
+        return el * 1e3
+
+    def grad_run(prec, seed_pw=None):
+        sim = sph.Simulation(sc, precision=prec, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.tape(n, dt)
+        t1 = time.perf_counter()
+        pw = sim.state()["pw"]
+        seed = {"pw": 2.0 * pw * mask if seed_pw is None else seed_pw}
+        t2 = time.perf_counter()
+        g = sim.backward(seed)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        sim.close()
+        return (t1 - t0) * 1e3, (t3 - t2) * 1e3, g, seed["pw"], float((pw * pw * mask).sum())
+
+    # per-kernel time of one taped forward + backward (CUDA events per launch;
+    # the recompute then runs kernel by kernel instead of as a graph)
+    sim = sph.Simulation(sc, precision=sph.SPH_FP32, stream=stream.cuda_stream)
+    sim.profile(sph.KERNEL_KINDS)
+    sim.tape(n, dt)
+    tape_prof = sim.profile_read()
+    sim.profile(sph.KERNEL_KINDS)
+    sim.backward({"pw": 2.0 * sim.state()["pw"] * mask})
+    bwd_prof = sim.profile_read()
+    sim.close()
+    kernel_ms = {"tape": {k: round(v["ms"], 4) for k, v in tape_prof.items() if v["timed"]},
+                 "backward": {k: round(v["ms"], 4) for k, v in bwd_prof.items() if v["timed"]}}
+
+    fwd = min(forward_ms() for _ in range(reps))
+    runs = [grad_run(sph.SPH_FP32) for _ in range(reps)]
+    tape_ms = min(r[0] for r in runs)
+    bwd_ms = min(r[1] for r in runs)
+    g32, loss32 = runs[0][2], runs[0][4]
+    _, _, g64, _, loss64 = grad_run(sph.SPH_FP64_PLAIN, seed_pw=runs[0][3])
+
+    def rel(a, b):
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+    return {"workload": "dam_break_adjoint_189k", "n_fluid": sc.n_fluid, "n_wall": sc.n_wall,
+            "steps": n, "dt": dt, "loss": "sum of p_w^2 over 64 probe walls behind the column",
+            "loss_fp32": loss32, "loss_fp64": loss64,
+            "forward_ms": fwd, "tape_ms": tape_ms, "backward_ms": bwd_ms,
+            "fwd_bwd_over_fwd": (tape_ms + bwd_ms) / fwd,
+            "timing": "host wall clock around the calls (each synchronises), best of 3",
+            "kernel_ms": kernel_ms,
+            "fp32_vs_fp64_grad_rel_err": {k: rel(g32[k], g64[k]) for k in ("x", "v", "rho")},
+            "fp32_vs_fp64_param_grad": {k: [g32[k], g64[k]] for k in ("c0", "gamma_p", "mu")}}
 
 
 def e2e(sc, steps, precision, stream, active_mean):

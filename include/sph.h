@@ -205,7 +205,11 @@ enum {
     SPH_K_WALL_PRESSURE = 7,/* wall dummy pressure, Eq. (wallPressure)        */
     SPH_K_MOMENTUM = 8,     /* momentum, penalty, viscosity, gravity, kick    */
     SPH_K_OTHER = 9,        /* create, export, diagnostics                    */
-    SPH_NK = 10
+    SPH_K_ADJ_MOMENTUM = 10,   /* backward of momentum and wall pressure      */
+    SPH_K_ADJ_CONTINUITY = 11, /* backward of continuity, kicks, reinit       */
+    SPH_K_ADJ_WALL = 12,       /* per-wall adjoints (2 launches per step)     */
+    SPH_K_ADJ_OTHER = 13,      /* seeds, permutation, prep, export, restores  */
+    SPH_NK = 14
 };
 
 /* Per-kernel timing with CUDA events recorded on the context's stream around

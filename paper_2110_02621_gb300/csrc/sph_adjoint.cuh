@@ -647,6 +647,35 @@ __global__ void k_adj_export(int32_t n, const int32_t* __restrict__ id, const V4
     if (orho) orho[k] = (double)x.w;
 }
 
+// Copy of up to 16 device arrays in one launch (checkpoint save / restore).
+// Sizes are in 4-byte words; every array starts 16-byte aligned (cudaMalloc
+// bases, 256-byte checkpoint slots), so whole 16-byte chunks move as uint4.
+struct CopySeg {
+    void* dst;
+    const void* src;
+    size_t words;
+};
+struct CopyList {
+    CopySeg seg[16];
+    int n;
+    size_t total;
+};
+
+static __global__ void k_copy_segments(CopyList L)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int s = 0; s < L.n; ++s) {
+        uint32_t* d = (uint32_t*)L.seg[s].dst;
+        const uint32_t* q = (const uint32_t*)L.seg[s].src;
+        const size_t n = L.seg[s].words, n4 = n / 4;
+        uint4* d4 = (uint4*)d;
+        const uint4* q4 = (const uint4*)q;
+        for (size_t k = t0; k < n4; k += stride) d4[k] = q4[k];
+        for (size_t k = 4 * n4 + t0; k < n; k += stride) d[k] = q[k];
+    }
+}
+
 static __global__ void k_bump_tag(int32_t* d_tag)
 {
     if (threadIdx.x == 0 && blockIdx.x == 0) *d_tag += 1;

@@ -294,6 +294,13 @@ class Sim final : public SimBase {
             if (s != SPH_OK) return s;
             ++steps_;
         }
+        return finish_steps(dt_out);
+    }
+
+    // read the error word, the in-grid count and the last dt after a run of
+    // steps (one synchronisation)
+    sph_status finish_steps(double* dt_out)
+    {
         SPH_CUDA(cudaMemcpyAsync(&host_status_->flags, d_flags_, sizeof(int32_t), cudaMemcpyDeviceToHost,
                                  stream));
         SPH_CUDA(cudaMemcpyAsync(&host_status_->n_in, fstart_ + n_cells_, sizeof(int32_t),
@@ -345,24 +352,31 @@ class Sim final : public SimBase {
             err = "untaped steps were taken since the last sph_tape";
             return SPH_ERR_STATE;
         }
-        double last = 0.0;
+        host_status_->dt_fixed = (T)(dt > 0.0 ? dt : 0.0);
+        SPH_CUDA(cudaMemcpyAsync(d_dt_fixed_, &host_status_->dt_fixed, sizeof(T), cudaMemcpyHostToDevice,
+                                 stream));
+        const int64_t first = ntaped_;
         for (int32_t k = 0; k < nsteps; ++k) {
-            // ck_[k] is the state before taped step k
+            // ck_[k] is the state before taped step k (copies ordered on the stream)
             if ((size_t)ntaped_ == ck_.size()) {
                 ck_.emplace_back();
                 sph_status s = save(ck_.back());
                 if (s != SPH_OK) return s;
             }
-            Ckpt& c = ck_[ntaped_];
+            Ckpt& c = ck_[(size_t)ntaped_];
             c.reinit = P_.reinit_every > 0 && (steps_ % P_.reinit_every) == 0;
-            sph_status s = step(1, dt, &last);
+            sph_status s = prof_mask_ ? one_step(c.reinit) : graph_step(c.reinit);
             if (s != SPH_OK) return s;
-            c.dt = host_status_->dt;
+            // the dt the step used, kept on the device for the recompute
+            SPH_CUDA(cudaMemcpyAsync(c.dtd, d_dt_, sizeof(T), cudaMemcpyDeviceToDevice, stream));
+            ++steps_;
             ++ntaped_;
             tape_end_ = steps_;
         }
-        if (dt_out) *dt_out = last;
-        return SPH_OK;
+        for (int64_t k = first; k < ntaped_; ++k)
+            SPH_CUDA(cudaMemcpyAsync(&ck_[(size_t)k].dt, ck_[(size_t)k].dtd, sizeof(T), cudaMemcpyDeviceToHost,
+                                     stream));
+        return finish_steps(dt_out);
     }
 
     sph_status backward(const sph_adjoint_seed& seed, sph_adjoint_grad& grad, int32_t where) override
@@ -401,50 +415,49 @@ class Sim final : public SimBase {
         SPH_CUDA(cudaMemsetAsync(adj_param_, 0, 3 * sizeof(double), stream));
         int cur = 0;  // adjoint state buffers in use
         if (nf_ > 0)
-            SPH_KERNEL(SPH_K_OTHER, 1,
+            SPH_KERNEL(SPH_K_ADJ_OTHER, 1,
                        k_adj_seed<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, id_[par_], sx, sv, srho, gx_[0],
                                                                          gv_[0], ga_[0]));
         if (nw_ > 0)
-            SPH_KERNEL(SPH_K_OTHER, 1,
+            SPH_KERNEL(SPH_K_ADJ_OTHER, 1,
                        k_adj_seed_wall<T><<<grid_for(nw_), BLOCK, 0, stream>>>(nw_, wid_, spw, gpw_[0]));
 
         for (int64_t k = ntaped_ - 1; k >= 0; --k) {
             const Ckpt& c = ck_[(size_t)k];
             if ((s = restore(c)) != SPH_OK) return s;
             // recompute the step bit-identically (same dt, same reinit)
-            host_status_->dt_fixed = c.dt;
-            SPH_CUDA(cudaMemcpyAsync(d_dt_fixed_, &host_status_->dt_fixed, sizeof(T), cudaMemcpyHostToDevice,
-                                     stream));
-            s = prof_mask_ ? one_step(c.reinit) : graph_step(c.reinit);
+            SPH_CUDA(cudaMemcpyAsync(d_dt_fixed_, c.dtd, sizeof(T), cudaMemcpyDeviceToDevice, stream));
+            // (momentum's outputs a', v', sigma' are not read by the backward)
+            s = prof_mask_ ? one_step(c.reinit, false) : graph_step(c.reinit, false);
             if (s != SPH_OK) return s;
             const int p = c.par, q = p ^ 1;
             const int nxt = cur ^ 1;
             const T dt = c.dt;
             if (nf_ > 0) {
-                SPH_KERNEL(SPH_K_OTHER, 1,
+                SPH_KERNEL(SPH_K_ADJ_OTHER, 1,
                            k_adj_inverse<<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, c.id, adj_inv_));
-                SPH_KERNEL(SPH_K_OTHER, 1,
+                SPH_KERNEL(SPH_K_ADJ_OTHER, 1,
                            k_adj_prep<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, T(0.5) * dt, gv_[cur], ga_[cur],
                                                                               tA_));
             }
             if (nw_ > 0)
-                SPH_KERNEL(SPH_K_OTHER, 1,
+                SPH_KERNEL(SPH_K_ADJ_WALL, 1,
                            k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
                                C_, nw_, fstart_, wpos_, wrho_, wnrm_, wcell_, wtag_, d_tag_, pos_[0], vel_[p], tA_,
                                gpw_[cur], wc_, adj_param_));
             if (nf_ > 0) {
-                SPH_KERNEL(SPH_K_OTHER, 1,
+                SPH_KERNEL(SPH_K_ADJ_MOMENTUM, 1,
                            k_adj_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                                C_, nf_, dt, 0, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_[p], drho_[0],
                                cell_[q], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], tX_, tV_, adj_param_));
-                SPH_KERNEL(SPH_K_OTHER, 1,
+                SPH_KERNEL(SPH_K_ADJ_CONTINUITY, 1,
                            k_adj_continuity<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                                C_, nf_, dt, c.reinit ? 1 : 0, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[1], vel_[p],
                                drho_[1], cell_[q], c.wpos, c.wrho, tX_, tV_, gx_[cur], id_[q], adj_inv_, c.drho,
                                c.sigma, gx_[nxt], gv_[nxt], ga_[nxt], adj_param_));
             }
             if (nw_ > 0)
-                SPH_KERNEL(SPH_K_OTHER, 1,
+                SPH_KERNEL(SPH_K_ADJ_WALL, 1,
                            k_adj_wall_continuity<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
                                C_, nw_, fstart_, c.wpos, c.wrho, wcell_, wtag_, d_tag_, pos_[1], vel_[p], drho_[1],
                                tX_, gpw_[nxt], adj_param_));
@@ -453,23 +466,23 @@ class Sim final : public SimBase {
 
         // the sweeps of sph_create at r^0: wall pressure, a^0, sigma^0
         if ((s = restore(ck_[0])) != SPH_OK) return s;
-        SPH_KERNEL(SPH_K_OTHER, 1, k_bump_tag<<<1, 32, 0, stream>>>(d_tag_));
+        SPH_KERNEL(SPH_K_ADJ_OTHER, 1, k_bump_tag<<<1, 32, 0, stream>>>(d_tag_));
         if ((s = neighbors(pos_[0], cell_[par_])) != SPH_OK) return s;
         const int p0 = par_;
         if (nf_ > 0)
-            SPH_KERNEL(SPH_K_OTHER, 1,
+            SPH_KERNEL(SPH_K_ADJ_OTHER, 1,
                        k_adj_prep<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, T(0), gv_[cur], ga_[cur], tA_));
         if (nw_ > 0)
-            SPH_KERNEL(SPH_K_OTHER, 1,
+            SPH_KERNEL(SPH_K_ADJ_WALL, 1,
                        k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
                            C_, nw_, fstart_, wpos_, wrho_, wnrm_, wcell_, wtag_, d_tag_, pos_[0], vel_[p0], tA_,
                            gpw_[cur], wc_, adj_param_));
         if (nf_ > 0) {
-            SPH_KERNEL(SPH_K_OTHER, 1,
+            SPH_KERNEL(SPH_K_ADJ_MOMENTUM, 1,
                        k_adj_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                            C_, nf_, T(0), 1, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_[p0], drho_[0],
                            cell_[p0], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], tX_, tV_, adj_param_));
-            SPH_KERNEL(SPH_K_OTHER, 1,
+            SPH_KERNEL(SPH_K_ADJ_OTHER, 1,
                        k_adj_export<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, id_[p0], tX_, tV_, ox, ov, orho));
         }
         SPH_CUDA(cudaMemcpyAsync(grad.params, adj_param_, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
@@ -744,7 +757,7 @@ class Sim final : public SimBase {
     //   continuity: pos[1], vel[q], drho[1] -> pos[0], vel[p], drho[0], acc.w
     //   wall pressure, momentum read pos[0], vel[p]; momentum writes vel[q]
     // so pos and drho stay in [0] while vel, comp, cell, id, phase alternate.
-    sph_status one_step(bool reinit)
+    sph_status one_step(bool reinit, bool with_momentum = true)
     {
         const int p = par_, q = par_ ^ 1;
         SPH_KERNEL(SPH_K_BEGIN_STEP, 1,
@@ -773,8 +786,10 @@ class Sim final : public SimBase {
         }
         sph_status s = wall_pressure(vel_[p]);
         if (s != SPH_OK) return s;
-        s = momentum(vel_[p], vel_[q], cell_[q], phase_[q]);
-        if (s != SPH_OK) return s;
+        if (with_momentum) {
+            s = momentum(vel_[p], vel_[q], cell_[q], phase_[q]);
+            if (s != SPH_OK) return s;
+        }
         par_ = q;
         return SPH_OK;
     }
@@ -784,9 +799,9 @@ class Sim final : public SimBase {
     // kernel argument, so up to four graphs exist, captured on first use on
     // an internal stream (the caller's may be the legacy default stream,
     // which cannot be captured) and launched on the caller's stream.
-    sph_status graph_step(bool reinit)
+    sph_status graph_step(bool reinit, bool with_momentum = true)
     {
-        const int key = (par_ << 1) | (reinit ? 1 : 0);
+        const int key = (with_momentum ? 0 : 4) | (par_ << 1) | (reinit ? 1 : 0);
         if (!gexec_[key]) {
             if (!cap_stream_) SPH_CUDA(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
             cudaStream_t user = stream;
@@ -795,7 +810,7 @@ class Sim final : public SimBase {
             memcpy(before, launches_, sizeof before);
             stream = cap_stream_;
             cudaError_t e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal);
-            sph_status s = e == cudaSuccess ? one_step(reinit) : SPH_OK;
+            sph_status s = e == cudaSuccess ? one_step(reinit, with_momentum) : SPH_OK;
             cudaGraph_t g = nullptr;
             cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap_stream_, &g) : e;
             stream = user;
@@ -823,7 +838,7 @@ class Sim final : public SimBase {
     struct Ckpt {
         char* buf = nullptr;
         V4<T>*pos = nullptr, *vel = nullptr, *acc = nullptr, *comp = nullptr, *wpos = nullptr;
-        T *drho = nullptr, *sigma = nullptr;
+        T *drho = nullptr, *sigma = nullptr, *dtd = nullptr;  // dtd: the step's dt (device)
         int4* cell = nullptr;
         int32_t *id = nullptr, *phase = nullptr, *fstart = nullptr;
         V2<T>* wrho = nullptr;
@@ -851,7 +866,7 @@ class Sim final : public SimBase {
                          o_ph = take(nf * sizeof(int32_t)), o_wpos = take(nw * sizeof(V4<T>)),
                          o_wrho = take(nw * sizeof(V2<T>)), o_vm = take(sizeof(unsigned long long)),
                          o_ac = take(sizeof(unsigned long long)),
-                         o_fs = take(((size_t)n_cells_ + 2) * sizeof(int32_t));
+                         o_fs = take(((size_t)n_cells_ + 2) * sizeof(int32_t)), o_dt = take(sizeof(T));
             sph_status s = alloc(c.buf, off);
             if (s != SPH_OK) return s;
             c.pos = (V4<T>*)(c.buf + o_pos);
@@ -868,58 +883,53 @@ class Sim final : public SimBase {
             c.vmax = (unsigned long long*)(c.buf + o_vm);
             c.active = (unsigned long long*)(c.buf + o_ac);
             c.fstart = (int32_t*)(c.buf + o_fs);
+            c.dtd = (T*)(c.buf + o_dt);
         }
-        const int p = par_;
-        auto cp = [&](void* dst, const void* src, size_t bytes) -> sph_status {
-            if (bytes) SPH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream));
-            return SPH_OK;
-        };
-        sph_status s;
-        if ((s = cp(c.pos, pos_[0], nf * sizeof(V4<T>))) != SPH_OK) return s;
-        if ((s = cp(c.vel, vel_[p], nf * sizeof(V4<T>))) != SPH_OK) return s;
-        if ((s = cp(c.acc, acc_, nf * sizeof(V4<T>))) != SPH_OK) return s;
-        if ((s = cp(c.comp, comp_[p], nf * sizeof(V4<T>))) != SPH_OK) return s;
-        if ((s = cp(c.drho, drho_[0], nf * sizeof(T))) != SPH_OK) return s;
-        if ((s = cp(c.sigma, sigma_, nf * sizeof(T))) != SPH_OK) return s;
-        if ((s = cp(c.cell, cell_[p], nf * sizeof(int4))) != SPH_OK) return s;
-        if ((s = cp(c.id, id_[p], nf * sizeof(int32_t))) != SPH_OK) return s;
-        if ((s = cp(c.phase, phase_[p], nf * sizeof(int32_t))) != SPH_OK) return s;
-        if ((s = cp(c.wpos, wpos_, nw * sizeof(V4<T>))) != SPH_OK) return s;
-        if ((s = cp(c.wrho, wrho_, nw * sizeof(V2<T>))) != SPH_OK) return s;
-        if ((s = cp(c.vmax, d_vmax_, sizeof(unsigned long long))) != SPH_OK) return s;
-        if ((s = cp(c.active, d_active_, sizeof(unsigned long long))) != SPH_OK) return s;
-        // cell ranges of the saved order (recomputed by a step, but read by the
-        // create-time sweeps and by sph_get_cells)
-        if ((s = cp(c.fstart, fstart_, ((size_t)n_cells_ + 2) * sizeof(int32_t))) != SPH_OK) return s;
-        c.par = p;
+        c.par = par_;
         c.steps = steps_;
+        return copy_ckpt(c, true);
+    }
+
+    // One launch copying every array of a checkpoint (to it when save, from
+    // it otherwise).  The cell ranges are included: a step recomputes them,
+    // but the create-time sweeps and sph_get_cells read them.
+    sph_status copy_ckpt(const Ckpt& c, bool save)
+    {
+        const size_t nf = (size_t)nf_, nw = (size_t)nw_;
+        const int p = c.par;
+        CopyList L{};
+        auto add = [&](void* state, void* ck, size_t bytes) {
+            CopySeg& g = L.seg[L.n++];
+            g.dst = save ? ck : state;
+            g.src = save ? state : ck;
+            g.words = bytes / 4;
+            L.total += g.words;
+        };
+        add(pos_[0], c.pos, nf * sizeof(V4<T>));
+        add(vel_[p], c.vel, nf * sizeof(V4<T>));
+        add(acc_, c.acc, nf * sizeof(V4<T>));
+        add(comp_[p], c.comp, nf * sizeof(V4<T>));
+        add(drho_[0], c.drho, nf * sizeof(T));
+        add(sigma_, c.sigma, nf * sizeof(T));
+        add(cell_[p], c.cell, nf * sizeof(int4));
+        add(id_[p], c.id, nf * sizeof(int32_t));
+        add(phase_[p], c.phase, nf * sizeof(int32_t));
+        add(wpos_, c.wpos, nw * sizeof(V4<T>));
+        add(wrho_, c.wrho, nw * sizeof(V2<T>));
+        add(d_vmax_, c.vmax, sizeof(unsigned long long));
+        add(d_active_, c.active, sizeof(unsigned long long));
+        add(fstart_, c.fstart, ((size_t)n_cells_ + 2) * sizeof(int32_t));
+        const int64_t want = (int64_t)((L.total / 4 + 255) / 256);
+        const int nb = (int)(want < 1 ? 1 : (want > 152 * 8 ? 152 * 8 : want));
+        SPH_KERNEL(SPH_K_ADJ_OTHER, 1, k_copy_segments<<<nb, 256, 0, stream>>>(L));
         return SPH_OK;
     }
 
     sph_status restore(const Ckpt& c)
     {
-        const size_t nf = (size_t)nf_, nw = (size_t)nw_;
-        const int p = c.par;
-        auto cp = [&](void* dst, const void* src, size_t bytes) -> sph_status {
-            if (bytes) SPH_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, stream));
-            return SPH_OK;
-        };
-        sph_status s;
-        if ((s = cp(pos_[0], c.pos, nf * sizeof(V4<T>))) != SPH_OK) return s;
-        if ((s = cp(vel_[p], c.vel, nf * sizeof(V4<T>))) != SPH_OK) return s;
-        if ((s = cp(acc_, c.acc, nf * sizeof(V4<T>))) != SPH_OK) return s;
-        if ((s = cp(comp_[p], c.comp, nf * sizeof(V4<T>))) != SPH_OK) return s;
-        if ((s = cp(drho_[0], c.drho, nf * sizeof(T))) != SPH_OK) return s;
-        if ((s = cp(sigma_, c.sigma, nf * sizeof(T))) != SPH_OK) return s;
-        if ((s = cp(cell_[p], c.cell, nf * sizeof(int4))) != SPH_OK) return s;
-        if ((s = cp(id_[p], c.id, nf * sizeof(int32_t))) != SPH_OK) return s;
-        if ((s = cp(phase_[p], c.phase, nf * sizeof(int32_t))) != SPH_OK) return s;
-        if ((s = cp(wpos_, c.wpos, nw * sizeof(V4<T>))) != SPH_OK) return s;
-        if ((s = cp(wrho_, c.wrho, nw * sizeof(V2<T>))) != SPH_OK) return s;
-        if ((s = cp(d_vmax_, c.vmax, sizeof(unsigned long long))) != SPH_OK) return s;
-        if ((s = cp(d_active_, c.active, sizeof(unsigned long long))) != SPH_OK) return s;
-        if ((s = cp(fstart_, c.fstart, ((size_t)n_cells_ + 2) * sizeof(int32_t))) != SPH_OK) return s;
-        par_ = p;
+        sph_status s = copy_ckpt(c, false);
+        if (s != SPH_OK) return s;
+        par_ = c.par;
         steps_ = c.steps;
         return SPH_OK;
     }
@@ -992,8 +1002,9 @@ class Sim final : public SimBase {
     int32_t* ncnt_ = nullptr;                  // per-lane entry counts
     int32_t *wtag_ = nullptr, *d_tag_ = nullptr;  // wall support tags, current tag
     cudaStream_t cap_stream_ = nullptr;
-    cudaGraphExec_t gexec_[4] = {nullptr, nullptr, nullptr, nullptr};
-    int64_t glaunch_[4][SPH_NK] = {};
+    // graphs keyed by (recompute without momentum, parity, reinit)
+    cudaGraphExec_t gexec_[8] = {};
+    int64_t glaunch_[8][SPH_NK] = {};
     int4* newcell_ = nullptr;
     int32_t *rank_ = nullptr, *tmp_src_ = nullptr, *tmp_id_ = nullptr;
     int32_t *counts_ = nullptr, *fstart_ = nullptr, *wstart_ = nullptr, *sums_ = nullptr;

@@ -149,14 +149,15 @@ def dam_break(tank: Tuple[float, float, float] = (1.6, 0.67, 0.6),
               column: Tuple[float, float, float] = (0.4, 0.67, 0.3),
               dp: float = 0.01, layers: int = 3, penalty: bool = True,
               reinit_every: int = 20, steps: int = 2000,
-              mu: float = 0.0, n_probes: int = 0) -> Scene:
+              mu: float = 0.0, n_probes: int = 0, probe_wall: str = "far") -> Scene:
     """Single-phase 3-D dam break: a water column at the x = 0 end of a box.
 
     Defaults: tank 1.6 x 0.67 x 0.6 m, column 0.4 x 0.67 x 0.3 m, dp = 0.01
     (80,400 fluid and 120,234 wall particles), penalty on, density
     reinitialisation every 20 steps.  With ``n_probes`` > 0 a square grid of
     probe wall particles is chosen on the inner layer of the far wall
-    (x = Lx side) over z in [0, column height].
+    (``probe_wall="far"``, x = Lx side) or of the wall behind the water column
+    (``"near"``, x = 0 side) over z in [0, column height].
     """
     ntx, nty, ntz = (_count(v, dp) for v in tank)
     ncx, ncy, ncz = (_count(v, dp) for v in column)
@@ -168,7 +169,7 @@ def dam_break(tank: Tuple[float, float, float] = (1.6, 0.67, 0.6),
     probes = None
     if n_probes > 0:
         side = int(round(math.sqrt(n_probes)))
-        x_in = ntx * dp + 0.5 * dp
+        x_in = ntx * dp + 0.5 * dp if probe_wall == "far" else -0.5 * dp
         cand = np.where(np.abs(wall[:, 0] - x_in) < 0.25 * dp)[0]
         cand = cand[(wall[cand, 2] > 0.0) & (wall[cand, 2] < H)
                     & (wall[cand, 1] > 0.0) & (wall[cand, 1] < nty * dp)]
@@ -348,7 +349,8 @@ def standard(name: str) -> Scene:
     if name == "two_phase_ramp_cylinder":
         return two_phase_ramp_cylinder()
     if name == "dam_break_adjoint_189k":
-        return dam_break(dp=0.0075, steps=10, n_probes=64)
+        # probes behind the column: the far wall sees no water within 10 steps
+        return dam_break(dp=0.0075, steps=10, n_probes=64, probe_wall="near")
     if name == "dam_break_10m":
         return dam_break(tank=(3.2, 1.0, 1.0), column=(1.2, 1.0, 0.55),
                          dp=0.004, steps=200)

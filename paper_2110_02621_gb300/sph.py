@@ -31,7 +31,8 @@ EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
 SPH_ERR_CAPACITY = 8
 SPH_BIN_SORT_NOALLOC_SCRATCH = 32 << 20
 KERNEL_KINDS = ("begin_step", "predict", "scan", "scatter", "gather", "neighbors",
-                "continuity", "wall_pressure", "momentum", "other")
+                "continuity", "wall_pressure", "momentum", "other", "adj_momentum",
+                "adj_continuity", "adj_wall", "adj_other")
 SPH_NK = len(KERNEL_KINDS)
 
 
