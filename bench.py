@@ -3,10 +3,11 @@
 Workload: the 3-D single-phase dam break (tank 1.6 x 0.67 x 0.6 m, water
 column 0.4 x 0.67 x 0.3 m, dp = 0.01 m: 80,400 fluid and 120,234 wall
 particles, Tait EOS, penalty on, density reinitialisation every 20 steps),
-FP32, synthetic lattice input.  One benchmark step = one sph_step time step
-(re-bin and sort, continuity, wall pressure, momentum, integration), timed
-with CUDA events on the library's stream, with a 256 MB write between steps
-so that every step starts with a cold L2.
+FP32, synthetic lattice input.  One benchmark step = one time step (re-bin
+and sort, continuity, wall pressure, momentum, integration) enqueued with
+sph_step_async, timed with CUDA events on the library's stream around it, with
+a 256 MB write between steps so that every step starts with a cold L2; the
+status of the timed steps is checked with sph_sync afterwards.
 
 Metric: M particle-steps/s, particles = fluid + wall particles with fluid
 support in that step.  One JSON line on stdout (rank 0).
@@ -160,10 +161,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# sources of the step's kernels (device functions, step kernels, pair sweeps,
+# scan); the recorded ncu traffic is void once any of them changes
+KERNEL_SOURCES = ("sph_device.cuh", "sph_kernels.cuh", "sph_sweeps.cuh", "sph_sort.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2110_02621_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -202,7 +208,7 @@ def cpu_baseline(sc, active_walls: float, seconds: float):
     t0 = time.perf_counter()
     sim.step(1)
     t1 = time.perf_counter() - t0
-    n = max(1, min(50, int(seconds / max(t1, 1e-3)) - 1))
+    n = max(1, min(2000, int(seconds / max(t1, 1e-3)) - 1))
     t0 = time.perf_counter()
     sim.step(n)
     el = time.perf_counter() - t0
@@ -308,10 +314,11 @@ def run_gpu(args):
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
-        sim.step(1)
+        sim.step_async(1)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     wall1 = time.perf_counter()
+    sim.sync()  # status of the timed steps
     if pg:
         pg.barrier()
     clk = clocks.stop()
@@ -330,7 +337,8 @@ def run_gpu(args):
     n_prof = min(args.steps, 200)
     for _ in range(n_prof):
         flush.zero_()
-        sim.step(1)
+        sim.step_async(1)
+    sim.sync()
     prof2 = sim.profile_read()
     dom_ms = prof2[dominant]["ms"] / max(prof2[dominant]["timed"], 1)
     sim.close()
@@ -419,9 +427,10 @@ def fp64_throughput(sc, steps, stream, flush):
     for k in range(steps):
         flush.zero_()
         ev[k][0].record(stream)
-        sim.step(1)
+        sim.step_async(1)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
+    sim.sync()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     s1, a1 = sim.counters()
     sim.close()

@@ -153,6 +153,19 @@ sph_status sph_create(const sph_params* params, const sph_fluid* fluid,
  * SPH_ERR_NONFINITE, SPH_ERR_CUDA, SPH_ERR_STATE. */
 sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double dt, double* dt_out);
 
+/* Enqueue nsteps steps like sph_step and return without waiting for them:
+ * the host can queue further work (an L2 flush, events, more steps) while
+ * the GPU runs.  Errors of the enqueued steps (SPH_ERR_DOMAIN,
+ * SPH_ERR_NONFINITE) are reported by the next sph_sync or sph_step.  A dt
+ * different from the previous call's waits for the stream first (the value
+ * travels through one pinned word).  Errors: SPH_ERR_ARG, SPH_ERR_CUDA,
+ * SPH_ERR_STATE. */
+sph_status sph_step_async(sph_ctx* ctx, int32_t nsteps, double dt);
+
+/* Wait for the enqueued steps and report their status as sph_step does;
+ * *dt_out (may be NULL) receives the last step's dt. */
+sph_status sph_sync(sph_ctx* ctx, double* dt_out);
+
 /* Reinitialise the fluid density now with the number density of the current
  * positions (Eqs. eqrhosum / eqrhosumnosurface per phase mode), and update
  * the pressure.  Errors: SPH_ERR_CUDA, SPH_ERR_STATE. */

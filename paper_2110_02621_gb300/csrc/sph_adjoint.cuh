@@ -316,10 +316,16 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
         const V4<T> pi = pos[i], vi = vel[i], Ai = tA[i];
         const int4 c = cell[i];
         const T rho_i = vi.w, p_i = pi.w, m = P.m;
-        const T pi_i = p_div(p_i, rho_i);
+        const T inv_rho_i = T(1) / rho_i;
+        const T pi_i = p_i * inv_rho_i;
         const T mu2 = T(2) * P.mu;
+        const bool visc = P.mu > T(0);
+        // pair sums of the adjoint of pi_i (sp), of pi_i's share of 1/(rho_i +
+        // rho_j) (spc) and of V's dependence on rho_i (svv), divided by rho_i
+        // once at the end
         T xx = T(0), xy = T(0), xz = T(0), ux = T(0), uy = T(0), uz = T(0), pb = T(0), rb = T(0);
-        T c0h = T(0), muh = T(0), c0f = T(0), muf = T(0), gpf = T(0);
+        T sp = T(0), spc = T(0), svv = T(0);
+        T c0h = T(0), muh = T(0), muf = T(0), gpf = T(0);
         for_neighbors(
             C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
             [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
@@ -327,8 +333,9 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
                 const T rinv = p_rsqrt(r2);
                 const T R = r2 * rinv;
                 const T F = kernel_F(C, R), Fp = kernel_dF(C, R);
-                const T rho_j = vj.w, pi_j = p_div(pj.w, rho_j);
-                const T rs = rho_i + rho_j;
+                const T inv_rho_j = p_div(T(1), vj.w);
+                const T pi_j = pj.w * inv_rho_j;
+                const T inv_rs = p_div(T(1), rho_i + vj.w);
                 const T vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
                 const T dU = -(rx * vx + ry * vy + rz * vz) * rinv;
                 T phi = T(0), dphi = T(0), dphic = T(0);
@@ -342,21 +349,25 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
                         dphic = dU;
                     }
                 }
-                const T Cc = p_div(pi_i + pi_j + phi, rs);
+                const T Cc = (pi_i + pi_j + phi) * inv_rs;
                 const T K = T(-2) * m * F * Cc;
-                const T e2 = r2 + C.eta2;
-                const T Q = p_div(r2 * F, e2);
-                const T dQ = p_div(T(2) * R * F * C.eta2 + r2 * Fp * e2, e2 * e2);
-                const T mv = p_div(m, rho_i * rho_j);
-                const T V = mu2 * mv * Q;
+                const T inv_e2 = p_div(T(1), r2 + C.eta2);
+                const T Q = r2 * F * inv_e2;
+                const T mv = m * inv_rho_i * inv_rho_j;
                 const T gx = Ai.x - Aj.x, gy = Ai.y - Aj.y, gz = Ai.z - Aj.z;
                 const T Kb = gx * rx + gy * ry + gz * rz;
                 const T Vb = gx * vx + gy * vy + gz * vz;
                 const T Fb = Kb * (T(-2) * m * Cc);
-                const T Cb = Kb * (T(-2) * m * F);
-                const T pib = p_div(Cb, rs);
+                const T pib = Kb * (T(-2) * m * F) * inv_rs;
                 const T Ub = pib * dphi;
-                const T Rb = Fb * Fp + Vb * mu2 * mv * dQ + (Ai.w + Aj.w) * F * R;
+                T Rb = Fb * Fp + (Ai.w + Aj.w) * F * R;
+                T V = T(0);
+                if (visc) {
+                    const T dQ = (T(2) * R * F * C.eta2 * inv_e2 + r2 * Fp) * inv_e2;
+                    V = mu2 * mv * Q;
+                    Rb += Vb * mu2 * mv * dQ;
+                    svv += Vb * V;
+                }
                 const T cr = Rb * rinv - Ub * dU * rinv * rinv;
                 const T cv = -Ub * rinv;
                 xx += K * gx + cr * rx + cv * vx;
@@ -365,8 +376,8 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
                 ux += V * gx + cv * rx;
                 uy += V * gy + cv * ry;
                 uz += V * gz + cv * rz;
-                pb += p_div(pib, rho_i);
-                rb += -pib * p_div(pi_i, rho_i) - pib * Cc - p_div(Vb * V, rho_i);
+                sp += pib;
+                spc += pib * Cc;
                 c0h += pib * dphic;
                 muh += Vb * T(2) * mv * Q;
             },
@@ -401,6 +412,8 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
                     xz += kg * C.gz + k * rz;
                 }
             });
+        pb += sp * inv_rho_i;
+        rb -= sp * pi_i * inv_rho_i + spc + svv * inv_rho_i;
         xx = group_sum(xx);
         xy = group_sum(xy);
         xz = group_sum(xz);
@@ -454,6 +467,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_continuity(
         const int4 c = cell[i];
         const T d_i = drho1[i];
         const T rho_i = P.rho0 + d_i, p_i = pi.w;
+        const T inv_rho_i = T(1) / rho_i;
         const T Di = tX[i].w;
         const T k = C.inv_c0, m2 = T(2) * P.m;
         T xx = T(0), xy = T(0), xz = T(0), ux = T(0), uy = T(0), uz = T(0), pb = T(0), rb = T(0), cb = T(0);
@@ -466,27 +480,28 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_continuity(
                 const T rinv = p_rsqrt(r2);
                 const T R = r2 * rinv;
                 const T F = kernel_F(C, R), Fp = kernel_dF(C, R);
-                const T rs = rho_i + rho_j;
-                const T A = p_div(m2, rs);
+                const T inv_rs = p_div(T(1), rho_i + rho_j);
+                const T inv_rho_j = p_div(T(1), rho_j);
+                const T A = m2 * inv_rs;
                 const T vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
                 const T S = rx * vx + ry * vy + rz * vz;
-                const T dp = p_i - p_j;
-                const T qj = p_div(dp * k, rho_j), qi = p_div(dp * k, rho_i);
+                const T dpk = (p_i - p_j) * k;
+                const T qj = dpk * inv_rho_j, qi = dpk * inv_rho_i;
                 const T Bij = S + qj * R, Bji = S - qi * R;
                 const T a = Di * rho_i, b = Dj * rho_j;
                 const T U = a * Bij + b * Bji;
-                const T E = A * F * U;
-                const T cr = A * (Fp * U * rinv + F * (a * qj - b * qi) * rinv);
-                const T cv = A * F * (a + b);
+                const T AF = A * F;
+                const T cr = A * (Fp * U + F * (a * qj - b * qi)) * rinv;
+                const T cv = AF * (a + b);
                 xx += cr * rx + cv * vx;
                 xy += cr * ry + cv * vy;
                 xz += cr * rz + cv * vz;
                 ux += cv * rx;
                 uy += cv * ry;
                 uz += cv * rz;
-                pb += A * F * R * k * (p_div(a, rho_j) - p_div(b, rho_i));
-                rb += -p_div(E, rs) + A * F * (Di * Bij + b * p_div(qi * R, rho_i));
-                cb -= a * A * F * qj * R * k;
+                pb += AF * R * k * (a * inv_rho_j - b * inv_rho_i);
+                rb += AF * (Di * Bij + b * qi * R * inv_rho_i - U * inv_rs);
+                cb -= a * AF * qj * R * k;
             },
             [&](int w, const V4<T>& pw, T rx, T ry, T rz, T r2) {
                 WallContAdj<T> o;

@@ -118,6 +118,23 @@ sph_status sph_step(sph_ctx* ctx, int32_t nsteps, double dt, double* dt_out)
     return ctx->sim->step(nsteps, dt, dt_out);
 }
 
+sph_status sph_step_async(sph_ctx* ctx, int32_t nsteps, double dt)
+{
+    sph_status s = usable(ctx);
+    if (s != SPH_OK) return s;
+    if (nsteps < 0 || !std::isfinite(dt)) {
+        ctx->sim->err = "nsteps must be >= 0 and dt finite";
+        return SPH_ERR_ARG;
+    }
+    return ctx->sim->step_async(nsteps, dt);
+}
+
+sph_status sph_sync(sph_ctx* ctx, double* dt_out)
+{
+    sph_status s = usable(ctx);
+    return s != SPH_OK ? s : ctx->sim->sync(dt_out);
+}
+
 sph_status sph_reinit_density(sph_ctx* ctx)
 {
     sph_status s = usable(ctx);

@@ -30,6 +30,8 @@ struct SimBase {
     virtual ~SimBase() {}
     virtual sph_status create(const sph_params& P, const sph_fluid& F, const sph_wall& W) = 0;
     virtual sph_status step(int32_t nsteps, double dt, double* dt_out) = 0;
+    virtual sph_status step_async(int32_t nsteps, double dt) = 0;
+    virtual sph_status sync(double* dt_out) = 0;
     virtual sph_status reinit() = 0;
     virtual sph_status get_state(const sph_state_out& o, int32_t where) = 0;
     virtual sph_status get_cells(uint32_t* kf, int32_t* of, int32_t* sf, uint32_t* kw, int32_t* ow,

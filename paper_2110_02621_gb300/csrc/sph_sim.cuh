@@ -281,11 +281,34 @@ class Sim final : public SimBase {
 
     sph_status step(int32_t nsteps, double dt, double* dt_out) override
     {
-        // pinned source; the previous call's copy has completed (each call ends
-        // with a stream synchronisation)
-        host_status_->dt_fixed = (T)(dt > 0.0 ? dt : 0.0);
+        sph_status s = enqueue_steps(nsteps, dt);
+        if (s != SPH_OK) return s;
+        return finish_steps(dt_out);
+    }
+
+    sph_status step_async(int32_t nsteps, double dt) override { return enqueue_steps(nsteps, dt); }
+
+    sph_status sync(double* dt_out) override { return finish_steps(dt_out); }
+
+    // The fixed dt reaches the device through a pinned word.  A copy from it
+    // may still be pending after an asynchronous call, so a new value first
+    // waits for the stream; an unchanged value is not copied again.
+    sph_status set_dt_fixed(double dt)
+    {
+        const T want = (T)(dt > 0.0 ? dt : 0.0);
+        if (dt_valid_ && want == host_status_->dt_fixed) return SPH_OK;
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        host_status_->dt_fixed = want;
         SPH_CUDA(cudaMemcpyAsync(d_dt_fixed_, &host_status_->dt_fixed, sizeof(T), cudaMemcpyHostToDevice,
                                  stream));
+        dt_valid_ = true;
+        return SPH_OK;
+    }
+
+    sph_status enqueue_steps(int32_t nsteps, double dt)
+    {
+        sph_status s0 = set_dt_fixed(dt);
+        if (s0 != SPH_OK) return s0;
         for (int32_t k = 0; k < nsteps; ++k) {
             bool reinit = P_.reinit_every > 0 && (steps_ % P_.reinit_every) == 0;
             // the kernel sequence of a step as one CUDA graph launch, unless
@@ -294,7 +317,7 @@ class Sim final : public SimBase {
             if (s != SPH_OK) return s;
             ++steps_;
         }
-        return finish_steps(dt_out);
+        return SPH_OK;
     }
 
     // read the error word, the in-grid count and the last dt after a run of
@@ -352,9 +375,8 @@ class Sim final : public SimBase {
             err = "untaped steps were taken since the last sph_tape";
             return SPH_ERR_STATE;
         }
-        host_status_->dt_fixed = (T)(dt > 0.0 ? dt : 0.0);
-        SPH_CUDA(cudaMemcpyAsync(d_dt_fixed_, &host_status_->dt_fixed, sizeof(T), cudaMemcpyHostToDevice,
-                                 stream));
+        sph_status s0 = set_dt_fixed(dt);
+        if (s0 != SPH_OK) return s0;
         const int64_t first = ntaped_;
         for (int32_t k = 0; k < nsteps; ++k) {
             // ck_[k] is the state before taped step k (copies ordered on the stream)
@@ -487,6 +509,7 @@ class Sim final : public SimBase {
         }
         SPH_CUDA(cudaMemcpyAsync(grad.params, adj_param_, 3 * sizeof(double), cudaMemcpyDeviceToHost, stream));
         if ((s = restore(snap_)) != SPH_OK) return s;
+        dt_valid_ = false;  // the recompute rewrote the device dt word
         if (where == SPH_HOST) {
             if (grad.x) SPH_CUDA(cudaMemcpyAsync(grad.x, ox, sizeof(double) * 3 * nf, cudaMemcpyDeviceToHost, stream));
             if (grad.v) SPH_CUDA(cudaMemcpyAsync(grad.v, ov, sizeof(double) * 3 * nf, cudaMemcpyDeviceToHost, stream));
@@ -1034,6 +1057,7 @@ class Sim final : public SimBase {
     double* adj_io_ = nullptr;
     double* adj_param_ = nullptr;
     HostStatus* host_status_ = nullptr;
+    bool dt_valid_ = false;  // d_dt_fixed_ holds host_status_->dt_fixed
     std::vector<void*> allocs_;
     uint32_t prof_mask_ = 0;
     bool prof_open_ = false;

@@ -27,7 +27,8 @@ _REINIT = {"none": 0, "free_surface": 1, "internal": 2}
 EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_grid_info", "sph_get_cells", "sph_diagnostics", "sph_counters",
            "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_bin_sort_noalloc",
-           "sph_profile", "sph_profile_read", "sph_tape", "sph_backward")
+           "sph_profile", "sph_profile_read", "sph_tape", "sph_backward", "sph_step_async",
+           "sph_sync")
 SPH_ERR_CAPACITY = 8
 SPH_BIN_SORT_NOALLOC_SCRATCH = 32 << 20
 KERNEL_KINDS = ("begin_step", "predict", "scan", "scatter", "gather", "neighbors",
@@ -113,6 +114,8 @@ def lib() -> C.CDLL:
         L.sph_profile.argtypes = [p, C.c_uint32]
         L.sph_profile_read.argtypes = [p, p, p, p]
         L.sph_tape.argtypes = [p, i32, d, p]
+        L.sph_step_async.argtypes = [p, i32, d]
+        L.sph_sync.argtypes = [p, p]
         L.sph_backward.argtypes = [p, p, p, i32]
         for name in EXPORTS:
             if name not in ("sph_last_error", "sph_destroy"):
@@ -244,6 +247,16 @@ def sph_profile_read(ctx):
     return st, ms, timed, launches
 
 
+def sph_step_async(ctx, nsteps: int, dt: float = 0.0):
+    return lib().sph_step_async(ctx, int(nsteps), float(dt))
+
+
+def sph_sync(ctx):
+    last = C.c_double(0.0)
+    st = lib().sph_sync(ctx, C.byref(last))
+    return st, last.value
+
+
 def sph_tape(ctx, nsteps: int, dt: float = 0.0):
     last = C.c_double(0.0)
     st = lib().sph_tape(ctx, int(nsteps), float(dt), C.byref(last))
@@ -297,6 +310,15 @@ class Simulation:
 
     def step(self, n: int = 1, dt: float = 0.0) -> float:
         st, last = sph_step(self.ctx, n, dt)
+        _check(st, self.ctx)
+        return last
+
+    def step_async(self, n: int = 1, dt: float = 0.0):
+        """Enqueue n steps without waiting (see sph_step_async)."""
+        _check(sph_step_async(self.ctx, n, dt), self.ctx)
+
+    def sync(self) -> float:
+        st, last = sph_sync(self.ctx)
         _check(st, self.ctx)
         return last
 

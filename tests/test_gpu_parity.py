@@ -313,3 +313,31 @@ def test_nonfinite_is_sticky():
         assert e.value.status == sph.SPH_ERR_NONFINITE
         st, _ = sph.sph_step(sim.ctx, 1, 1e-4)
         assert st == sph.SPH_ERR_STATE
+
+
+def test_step_async_matches_step_and_reports_at_sync():
+    """Enqueued steps (sph_step_async) give the state of sph_step bit for bit,
+    also across a change of dt; their errors surface at sph_sync."""
+    sc = small_dam()
+    with sph.Simulation(sc) as a, sph.Simulation(sc) as b:
+        a.step_async(3, 1e-4)
+        a.step_async(2, 2e-4)
+        a.step_async(2)
+        assert a.sync() > 0
+        b.step(3, 1e-4)
+        b.step(2, 2e-4)
+        b.step(2)
+        sa, sb = a.state(), b.state()
+        for k in ("x", "v", "rho", "p", "a", "pw"):
+            assert np.array_equal(sa[k], sb[k]), k
+    blob = S.jittered_blob(n=(6, 6, 6), vel_scale=0.0, margin_cells=3)
+    lone = np.array([[blob.lo[0] + 0.3 * 2 * blob.h, blob.fluid_pos[:, 1].mean(),
+                      blob.fluid_pos[:, 2].mean()]])
+    blob.fluid_pos = np.concatenate([lone, blob.fluid_pos])
+    blob.fluid_vel = np.zeros_like(blob.fluid_pos)
+    blob.fluid_vel[0] = [-5.0, 0.0, 0.0]
+    blob.fluid_phase = np.zeros(blob.n_fluid, np.int32)
+    with sph.Simulation(blob) as sim:
+        assert sph.sph_step_async(sim.ctx, 40, 2e-4) == sph.SPH_OK
+        st, _ = sph.sph_sync(sim.ctx)
+        assert st == sph.SPH_ERR_DOMAIN
