@@ -396,6 +396,7 @@ def run_gpu(args):
         line["fp64_plain"] = fp64_throughput(sc, min(args.steps, 200), stream, flush)
         line["accuracy"] = accuracy(sc)
         line["adjoint"] = adjoint_block(stream)
+        line["other_workloads"] = other_workloads(stream, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, active_mean, args.cpu_seconds)
     if rank == 0:
@@ -540,6 +541,48 @@ def adjoint_block(stream, reps: int = 3):
             "kernel_ms": kernel_ms,
             "fp32_vs_fp64_grad_rel_err": {k: rel(g32[k], g64[k]) for k in ("x", "v", "rho")},
             "fp32_vs_fp64_param_grad": {k: [g32[k], g64[k]] for k in ("c0", "gamma_p", "mu")}}
+
+
+def other_workloads(stream, flush, steps: int = 50):
+    """FP32 throughput of the two larger configurations (same step, same
+    timing method, fewer steps): the two-phase ramp/cylinder tank and the
+    10.35 M-particle dam break."""
+    import torch
+    from paper_2110_02621_gb300 import scenes, sph
+    out = {}
+    for name in ("two_phase_ramp_cylinder", "dam_break_10m"):
+        try:
+            sc = scenes.standard(name)
+            sim = sph.Simulation(sc, precision=sph.SPH_FP32, stream=stream.cuda_stream)
+            for _ in range(3):
+                flush.zero_()
+                sim.step(1)
+            s0, a0 = sim.counters()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(steps)]
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                sim.step_async(1)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            sim.sync()
+            t_ms = sum(a.elapsed_time(b) for a, b in ev)
+            s1, a1 = sim.counters()
+            sim.profile(sph.KERNEL_KINDS)
+            sim.step(3)
+            prof = sim.profile_read()
+            sim.close()
+            active = (a1 - a0) / max(s1 - s0, 1)
+            out[name] = {"n_fluid": sc.n_fluid, "n_wall": sc.n_wall, "active_wall_mean": round(active, 1),
+                         "ms_per_step": t_ms / steps, "steps": steps,
+                         "value": (sc.n_fluid + active) * steps / (t_ms / 1e3) / 1e6,
+                         "value_fluid_only": sc.n_fluid * steps / (t_ms / 1e3) / 1e6, "unit": UNIT,
+                         "kernel_us_per_step": {k: round(v["ms"] * 1e3 / 3, 1) for k, v in prof.items()
+                                                if v["timed"]}}
+        except Exception as e:  # reported, not fatal: the main line stands on its own
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def e2e(sc, steps, precision, stream, active_mean):

@@ -154,6 +154,35 @@ def test_create_parity_full_size_dam_break():
     check_state(g5, ref.fluid(), ref.wall(), sc.dp, what="5 steps")
 
 
+@pytest.mark.parametrize("name,nsteps", [("two_phase_ramp_cylinder", 2), ("dam_break_10m", 1)],
+                         ids=["two_phase_1.7M", "dam_break_10.35M"])
+def test_full_size_parity(name, nsteps):
+    """The two-phase ramp/cylinder tank (1,688,920 fluid, 359,062 wall) and the
+    large dam break (10,350,000 fluid, 2,203,008 wall) at full size, in the
+    library's own launch configuration: cells bit-exact, every field of the
+    created state, then positions and densities after a few CFL steps."""
+    sc = S.standard(name)
+    ref = oracle.OracleSim(sc)
+    light = np.array([sc.phases[p].density == "summation" for p in range(len(sc.phases))])[sc.fluid_phase]
+    with sph.Simulation(sc) as sim:
+        check_cells(sim, ref)
+        g = sim.state()
+        check_state(g, ref.fluid(), ref.wall(), sc.dp, what="create", light=light, floor=light_floor(sc))
+        d0 = sim.diagnostics()
+        dt = sim.step(nsteps)
+        g = sim.state()
+        d = sim.diagnostics()
+    dref = ref.step(nsteps)
+    assert abs(dt - dref) <= 1e-6 * dref
+    o = ref.fluid()
+    assert np.abs(g["x"] - o["x"]).max() <= TOL_X * sc.dp
+    assert rel_inf(g["rho"], o["rho"]) <= 1e-5
+    # mass: exactly conserved; against the oracle within the FP32 rounding of m
+    assert d[0] == d0[0]
+    assert d[0] == pytest.approx(ref.diagnostics()[0], rel=1e-7)
+    assert d[7] == 0
+
+
 # --------------------------------------------------------------- stepping
 @pytest.mark.parametrize("make", [lambda: S.still_water_tank(n_fluid=(10, 10, 10), wall_height=0.15),
                                   lambda: small_dam(),
