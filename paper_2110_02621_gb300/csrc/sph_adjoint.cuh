@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
         if (live) {
             const V4<T> nn = wnrm[w];
             const int4 c = wcell[w];
-            scan_share(C, c, pw, fstart, pos, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact(C, c, pw, fstart, pos, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 // scan vector is x_w - x_f; the pair vector of the fluid is x_f - x_w
                 const V4<T> pf = pos[j], vf = vel[j], Aj = tA[j];
                 WallMomAdj<T> o;
@@ -586,7 +586,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_continuity(
         T Gp = T(0), Gr = T(0), Gc = T(0);
         if (live) {
             const int4 c = wcell[w];
-            scan_share(C, c, pw, fstart, pos1, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact(C, c, pw, fstart, pos1, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 const V4<T> pf = pos1[j], vf = vel[j];
                 WallContAdj<T> o;
                 wall_continuity_adj(C, P, -rx, -ry, -rz, r2, vf.x, vf.y, vf.z, P.rho0 + drho1[j], pf.w, rho_w,

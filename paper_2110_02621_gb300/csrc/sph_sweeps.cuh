@@ -137,6 +137,88 @@ __device__ __forceinline__ void scan_share(const Cfg<T>& C, const int4& c, const
     }
 }
 
+// scan_share for the list builder: each row's three cells in turn with a
+// constant x shift (fewer instructions per candidate; larger code).
+// Lane l's share (every LP-th candidate) of the 27 cells around cell c of a
+// sorted set with cell ranges start[]: fn(j, rx, ry, rz, r2, code) for every
+// candidate with 0 < r^2 < (2h)^2, o = the target's offset, code = the
+// 6-bit cell shift of j.
+template <class T, class Fn>
+__device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const V4<T>& o,
+                                           const int32_t* __restrict__ start, const V4<T>* __restrict__ pts,
+                                           int l, Fn&& fn)
+{
+    const int xa = c.x > 0 ? c.x - 1 : 0;
+    const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
+    const T xl = o.x + C.cs, xr = o.x - C.cs;  // o_x - dx cs for dx = -1, +1
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int z = c.z + dz;
+        if (z < 0 || z >= C.nz) continue;
+        const T zs = o.z - T(dz) * C.cs;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int y = c.y + dy;
+            if (y < 0 || y >= C.ny) continue;
+            const T ys = o.y - T(dy) * C.cs;
+            const int row = (z * C.ny + y) * C.nx;
+            const int b = __ldg(start + row + xa), e = __ldg(start + row + xb + 1);
+            const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
+            const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
+            // the row's three cells in turn, each with its constant x shift;
+            // j runs on across them, so the lanes' shares stay interleaved
+            int j = b + l;
+            auto segment = [&](int end, T xs, int code) {
+#pragma unroll 4
+                for (; j < end; j += LP) {
+                    const V4<T> pj = pts[j];
+                    const T rx = xs - pj.x, ry = ys - pj.y, rz = zs - pj.z;
+                    const T r2 = dist2(rx, ry, rz);
+                    if (r2 < C.rc2 && r2 > T(0)) fn(j, rx, ry, rz, r2, code);
+                }
+            };
+            segment(b1, xl, cyz);
+            segment(b2, o.x, cyz | 1);
+            segment(e, xr, cyz | 2);
+        }
+    }
+}
+
+// The same candidates as scan_share in a compact loop (one loop per row, the
+// x shift chosen per candidate, no unrolling): for the rare fall-back scans of
+// over-full sub-lists and for the per-wall kernels, where code size and
+// registers matter more than the last instruction per candidate.
+template <class T, class Fn>
+__device__ __forceinline__ void scan_compact(const Cfg<T>& C, const int4& c, const V4<T>& o,
+                                             const int32_t* __restrict__ start, const V4<T>* __restrict__ pts,
+                                             int l, Fn&& fn)
+{
+    const int xa = c.x > 0 ? c.x - 1 : 0;
+    const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
+    const T xl = o.x + C.cs, xr = o.x - C.cs;
+    for (int dz = -1; dz <= 1; ++dz) {
+        const int z = c.z + dz;
+        if (z < 0 || z >= C.nz) continue;
+        const T zs = o.z - T(dz) * C.cs;
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int y = c.y + dy;
+            if (y < 0 || y >= C.ny) continue;
+            const T ys = o.y - T(dy) * C.cs;
+            const int row = (z * C.ny + y) * C.nx;
+            const int b = __ldg(start + row + xa), e = __ldg(start + row + xb + 1);
+            const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
+            const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
+#pragma unroll 1
+            for (int j = b + l; j < e; j += LP) {
+                const V4<T> pj = pts[j];
+                const int dxc = j < b1 ? 0 : (j < b2 ? 1 : 2);  // dx + 1
+                const T rx = (dxc == 0 ? xl : (dxc == 1 ? o.x : xr)) - pj.x;
+                const T ry = ys - pj.y, rz = zs - pj.z;
+                const T r2 = dist2(rx, ry, rz);
+                if (r2 < C.rc2 && r2 > T(0)) fn(j, rx, ry, rz, r2, cyz | dxc);
+            }
+        }
+    }
+}
+
 // --------------------------------------------------------- neighbour lists
 template <class T>
 __global__ void __launch_bounds__(LBLOCK) k_neighbors(
@@ -155,13 +237,13 @@ __global__ void __launch_bounds__(LBLOCK) k_neighbors(
         const int tag = *d_tag;
         const size_t stride = (size_t)n * LP;
         size_t at = t;
-        scan_share(C, c, o, fstart, pos, l, [&](int j, T, T, T, T, int code) {
+        scan_rows(C, c, o, fstart, pos, l, [&](int j, T, T, T, T, int code) {
             if (nf < SUBF) nbf[at] = (j << 6) | code;
             at += stride;
             ++nf;
         });
         at = t;
-        scan_share(C, c, o, wstart, wpos, l, [&](int w, T, T, T, T, int code) {
+        scan_rows(C, c, o, wstart, wpos, l, [&](int w, T, T, T, T, int code) {
             if (nw < SUBW) nbw[at] = (w << 6) | code;
             at += stride;
             ++nw;
@@ -324,7 +406,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
         if (wtag[w] == *d_tag) {
             const int4 c = wcell[w];
             const V4<T> pw = wpos[w];
-            scan_share(C, c, pw, fstart, pos, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact(C, c, pw, fstart, pos, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 const T W = kernel_W(C, r2 * p_rsqrt(r2));
                 const T p_f = reinterpret_cast<const T*>(pos + j)[3];
                 const T rho_f = vel[j].w;
