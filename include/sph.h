@@ -199,6 +199,15 @@ sph_status sph_get_cells(sph_ctx* ctx, uint32_t* key_fluid, int32_t* order_fluid
  * number of particles outside the grid}.  Synchronises. */
 sph_status sph_diagnostics(sph_ctx* ctx, double out[8]);
 
+/* The same reductions enqueued on the stream without waiting: the 8 values
+ * are copied to out when the stream reaches them (valid after sph_sync or
+ * any synchronising call).  where = SPH_DEVICE: out is device memory;
+ * SPH_HOST: out must be page-locked host memory (SPH_ERR_ARG otherwise), so
+ * that the copy does not block the host.  Successive calls may target
+ * different buffers (a ring of per-step results).  Errors: SPH_ERR_ARG,
+ * SPH_ERR_CUDA, SPH_ERR_STATE. */
+sph_status sph_diagnostics_async(sph_ctx* ctx, double* out, int32_t where);
+
 /* Counters since creation: steps taken and the summed number of wall
  * particles that had fluid support in each step's wall-pressure sweep.
  * Either pointer may be NULL.  Synchronises. */

@@ -175,6 +175,25 @@ sph_status sph_diagnostics(sph_ctx* ctx, double out[8])
     return ctx->sim->diagnostics(out);
 }
 
+sph_status sph_diagnostics_async(sph_ctx* ctx, double* out, int32_t where)
+{
+    sph_status s = usable(ctx);
+    if (s != SPH_OK) return s;
+    if (!out || (where != SPH_HOST && where != SPH_DEVICE)) {
+        ctx->sim->err = "out must not be NULL; where must be SPH_HOST or SPH_DEVICE";
+        return SPH_ERR_ARG;
+    }
+    if (where == SPH_HOST) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, out) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            ctx->sim->err = "out must be page-locked host memory (cudaHostAlloc / pinned)";
+            return SPH_ERR_ARG;
+        }
+    }
+    return ctx->sim->diagnostics_async(out, where);
+}
+
 sph_status sph_counters(sph_ctx* ctx, int64_t* steps, int64_t* active_wall_steps)
 {
     sph_status s = usable(ctx);

@@ -15,8 +15,10 @@ namespace sph {
 int32_t scan_blocks(int64_t n);
 int64_t scan_max_len();
 // out[0..n] = exclusive prefix sums of in[0..n-1] (out[n] = total);
-// sums needs scan_blocks(n) entries.
-void scan_exclusive(const int32_t* in, int32_t n, int32_t* out, int32_t* sums, cudaStream_t st);
+// sums needs scan_blocks(n) entries; clear (NULL or in) is zeroed behind the
+// scan.  Returns the number of kernels launched.
+int scan_exclusive(const int32_t* in, int32_t n, int32_t* out, int32_t* sums, cudaStream_t st,
+                   int32_t* clear);
 
 struct BinSortScratch {
     size_t cell, id, rank, tmp_src, tmp_id, counts, start, sums, bytes;
@@ -37,6 +39,7 @@ struct SimBase {
     virtual sph_status get_cells(uint32_t* kf, int32_t* of, int32_t* sf, uint32_t* kw, int32_t* ow,
                                  int32_t* sw) = 0;
     virtual sph_status diagnostics(double out[8]) = 0;
+    virtual sph_status diagnostics_async(double* out, int32_t where) = 0;
     virtual sph_status counters(int64_t* steps, int64_t* active) = 0;
     virtual void grid(int32_t dims[3], int64_t* n_cells, double* cs) const = 0;
     virtual sph_status profile(uint32_t mask) = 0;

@@ -35,10 +35,24 @@ __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <class T>
 __device__ __forceinline__ T tabs(T a) { return a < T(0) ? -a : a; }
 
+// dt of the coming step (Sec. 2.6): the caller's fixed dt, or
+// cfl min(h/(c0 + U_max), sqrt(h/|g|)) from the previous momentum sweep's U_max
+template <class T>
+__device__ __forceinline__ T step_dt(const Cfg<T>& C, const T* dt_fixed, const unsigned long long* vmax_bits)
+{
+    T dt = *dt_fixed;
+    if (!(dt > T(0))) {
+        const T umax = bits_to<T>(*vmax_bits);
+        dt = C.cfl * C.h / (C.c0 + umax);
+        if (C.body_dt > T(0)) dt = tmin(dt, C.body_dt);
+    }
+    return dt;
+}
+
 // --------------------------------------------------------------- step start
-// Time step (Sec. 2.6): dt = cfl min(h/(c0 + U_max), sqrt(h/|g|)) from the
-// U_max of the previous momentum sweep, unless a fixed dt > 0 is given.
-// Also clears the per-cell counters of the coming re-binning.
+// Step start for a context without fluid (with fluid, k_predict and k_scatter
+// do this): the step's dt, the wall-support tag, U_max and the per-cell
+// counters of the coming re-binning.
 template <class T>
 __global__ void k_begin_step(Cfg<T> C, const T* __restrict__ dt_fixed, unsigned long long* vmax_bits,
                              T* d_dt, int32_t* counts, int32_t n_counts, int32_t* d_tag)
@@ -46,13 +60,7 @@ __global__ void k_begin_step(Cfg<T> C, const T* __restrict__ dt_fixed, unsigned 
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
         *d_tag += 1;  // new wall-support tag for this step's neighbour build
-        T dt = *dt_fixed;
-        if (!(dt > T(0))) {
-            T umax = bits_to<T>(*vmax_bits);
-            dt = C.cfl * C.h / (C.c0 + umax);
-            if (C.body_dt > T(0)) dt = tmin(dt, C.body_dt);
-        }
-        *d_dt = dt;
+        *d_dt = step_dt(C, dt_fixed, vmax_bits);
         *vmax_bits = 0ull;
     }
     for (int k = t; k < n_counts; k += gridDim.x * blockDim.x) counts[k] = 0;
@@ -78,15 +86,24 @@ __device__ __forceinline__ void kick_drift(const Cfg<T>& C, T dt, V4<T>& p, V4<T
 
 // v^{n+1/2} = v^n + dt/2 a^n, r^{n+1} = r^n + dt v^{n+1/2} (Sec. 2.6), new cell
 // and its occupancy count; bucket n_cells collects particles outside the grid.
+// Every thread evaluates the step's dt; thread 0 publishes it for the later
+// kernels and opens the step's wall-support tag.  (U_max is cleared by the
+// scatter that follows, once every thread here has read it.)
 template <class T, bool KAHAN>
 __global__ void k_predict(Cfg<T> C, int32_t n, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel,
                           const V4<T>* __restrict__ acc, const V4<T>* __restrict__ comp,
-                          const int4* __restrict__ cell, const T* __restrict__ d_dt,
-                          int4* __restrict__ newcell, int32_t* __restrict__ rank, int32_t* counts)
+                          const int4* __restrict__ cell, const T* __restrict__ dt_fixed,
+                          const unsigned long long* __restrict__ vmax_bits, T* __restrict__ d_dt,
+                          int32_t* __restrict__ d_tag, int4* __restrict__ newcell, int32_t* __restrict__ rank,
+                          int32_t* counts)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    T dt = *d_dt;
+    const T dt = step_dt(C, dt_fixed, vmax_bits);
+    if (s == 0) {
+        *d_dt = dt;
+        *d_tag += 1;
+    }
     V4<T> p = pos[s], v = vel[s], a = acc[s], cm = comp[s];
     int4 c = cell[s];
     kick_drift<T, KAHAN>(C, dt, p, v, a, cm, c);
@@ -97,14 +114,16 @@ __global__ void k_predict(Cfg<T> C, int32_t n, const V4<T>* __restrict__ pos, co
     newcell[s] = c;
 }
 
-// first placement: slot = start of the bucket + arrival rank.
+// first placement: slot = start of the bucket + arrival rank.  In a step,
+// thread 0 also clears U_max for the coming momentum sweep (vmax_reset).
 static __global__ void k_scatter(int32_t n, int32_t n_cells, const int4* __restrict__ newcell,
                                  const int32_t* __restrict__ rank, const int32_t* __restrict__ start,
                                  const int32_t* __restrict__ id, int32_t* __restrict__ tmp_src,
-                                 int32_t* __restrict__ tmp_id)
+                                 int32_t* __restrict__ tmp_id, unsigned long long* vmax_reset)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
+    if (s == 0 && vmax_reset) *vmax_reset = 0ull;
     int key = newcell[s].w;
     int t = start[key < 0 ? n_cells : key] + rank[s];
     tmp_src[t] = s;

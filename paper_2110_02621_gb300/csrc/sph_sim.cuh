@@ -185,11 +185,11 @@ class Sim final : public SimBase {
                                                                 wid_tmp_, rank_, counts_);
             SPH_LAUNCH();
         }
-        scan_exclusive(counts_, n_cells_ + 1, wstart_, sums_, stream);
+        scan_exclusive(counts_, n_cells_ + 1, wstart_, sums_, stream, counts_);
         SPH_LAUNCH();
         if (nw_ > 0) {
             k_scatter<<<grid_for(nw_), BLOCK, 0, stream>>>(nw_, n_cells_, wcell_tmp_, rank_, wstart_,
-                                                           wid_tmp_, tmp_src_, tmp_id_);
+                                                           wid_tmp_, tmp_src_, tmp_id_, nullptr);
             k_gather_wall<T><<<grid_for(nw_), BLOCK, 0, stream>>>(nw_, n_cells_, wstart_, tmp_src_, tmp_id_,
                                                                   wpos_tmp_, wcell_tmp_, xw_in, wpos_, wcell_,
                                                                   wid_, xw_sorted);
@@ -236,11 +236,11 @@ class Sim final : public SimBase {
                 id_[0], phase_[0], rank_, counts_);
             SPH_LAUNCH();
         }
-        scan_exclusive(counts_, n_cells_ + 1, fstart_, sums_, stream);
+        scan_exclusive(counts_, n_cells_ + 1, fstart_, sums_, stream, counts_);
         SPH_LAUNCH();
         if (nf_ > 0) {
             k_scatter<<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, n_cells_, newcell_, rank_, fstart_, id_[0],
-                                                           tmp_src_, tmp_id_);
+                                                           tmp_src_, tmp_id_, nullptr);
             // dt = 0 and no reinitialisation: a pure permutation into (key, id) order
             k_gather<T, KAHAN><<<grid_for(nf_), BLOCK, 0, stream>>>(
                 C_, nf_, fstart_, tmp_src_, tmp_id_, newcell_, d_dt_, 0, pos_[0], vel_[0], drho_[0], acc_,
@@ -629,15 +629,24 @@ class Sim final : public SimBase {
 
     sph_status diagnostics(double out[8]) override
     {
-        int nb = grid_for(nf_ > 0 ? nf_ : 1);
-        k_diag_partial<T><<<nb, BLOCK, 0, stream>>>(C_, I_, nf_, pos_[0], vel_[par_], cell_[par_], phase_[par_],
-                                                    diag_partial_);
-        k_diag_final<<<1, 32, 0, stream>>>(nb, diag_partial_, diag_out_);
-        SPH_LAUNCH();
-        SPH_CUDA(cudaMemcpyAsync(host_status_->diag, diag_out_, sizeof(double) * 8, cudaMemcpyDeviceToHost,
-                                 stream));
+        sph_status s = diagnostics_async(host_status_->diag, SPH_HOST);
+        if (s != SPH_OK) return s;
         SPH_CUDA(cudaStreamSynchronize(stream));
         memcpy(out, host_status_->diag, sizeof(double) * 8);
+        return SPH_OK;
+    }
+
+    // the reductions and the copy of their 8 results to out (device memory,
+    // or page-locked host memory), enqueued on the stream
+    sph_status diagnostics_async(double* out, int32_t where) override
+    {
+        int nb = grid_for(nf_ > 0 ? nf_ : 1);
+        SPH_KERNEL(SPH_K_OTHER, 1,
+                   k_diag_partial<T><<<nb, BLOCK, 0, stream>>>(C_, I_, nf_, pos_[0], vel_[par_], cell_[par_],
+                                                               phase_[par_], diag_partial_));
+        SPH_KERNEL(SPH_K_OTHER, 1, k_diag_final<<<1, 32, 0, stream>>>(nb, diag_partial_, diag_out_));
+        SPH_CUDA(cudaMemcpyAsync(out, diag_out_, sizeof(double) * 8,
+                                 where == SPH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, stream));
         return SPH_OK;
     }
 
@@ -783,18 +792,24 @@ class Sim final : public SimBase {
     sph_status one_step(bool reinit, bool with_momentum = true)
     {
         const int p = par_, q = par_ ^ 1;
-        SPH_KERNEL(SPH_K_BEGIN_STEP, 1,
-                   k_begin_step<T><<<grid_for(n_cells_ + 1), BLOCK, 0, stream>>>(C_, d_dt_fixed_, d_vmax_, d_dt_,
-                                                                                counts_, n_cells_ + 1, d_tag_));
+        // the step's dt and wall tag come from k_predict, the U_max reset from
+        // k_scatter, and the scan leaves the cell counters cleared; without
+        // fluid a small kernel does all of it
         if (nf_ > 0)
             SPH_KERNEL(SPH_K_PREDICT, 1,
                        k_predict<T, KAHAN><<<grid_for(nf_), BLOCK, 0, stream>>>(
-                           C_, nf_, pos_[0], vel_[p], acc_, comp_[p], cell_[p], d_dt_, newcell_, rank_, counts_));
-        SPH_KERNEL(SPH_K_SCAN, 3, scan_exclusive(counts_, n_cells_ + 1, fstart_, sums_, stream));
+                           C_, nf_, pos_[0], vel_[p], acc_, comp_[p], cell_[p], d_dt_fixed_, d_vmax_, d_dt_, d_tag_,
+                           newcell_, rank_, counts_));
+        else
+            SPH_KERNEL(SPH_K_BEGIN_STEP, 1,
+                       k_begin_step<T><<<grid_for(n_cells_ + 1), BLOCK, 0, stream>>>(
+                           C_, d_dt_fixed_, d_vmax_, d_dt_, counts_, n_cells_ + 1, d_tag_));
+        int nscan = 0;
+        SPH_KERNEL(SPH_K_SCAN, nscan, nscan = scan_exclusive(counts_, n_cells_ + 1, fstart_, sums_, stream, counts_));
         if (nf_ > 0) {
             SPH_KERNEL(SPH_K_SCATTER, 1,
                        k_scatter<<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, n_cells_, newcell_, rank_, fstart_,
-                                                                      id_[p], tmp_src_, tmp_id_));
+                                                                      id_[p], tmp_src_, tmp_id_, d_vmax_));
             SPH_KERNEL(SPH_K_GATHER, 1,
                        k_gather<T, KAHAN><<<grid_for(nf_), BLOCK, 0, stream>>>(
                            C_, nf_, fstart_, tmp_src_, tmp_id_, newcell_, d_dt_, reinit ? 1 : 0, pos_[0], vel_[p],

@@ -1,8 +1,10 @@
 // Counting sort of particles by cell key (Sec. 3, "neighbour search
 // including sorting"): exclusive scan of the per-cell counts, first
 // placement by arrival rank, then the in-cell rank by particle id makes the
-// final order (key, id) independent of atomic arrival order.  The scan is a
-// three-kernel reduce / scan-of-sums / down-sweep with no inter-block waits.
+// final order (key, id) independent of atomic arrival order.  The scan is one
+// block for short inputs, else a three-kernel reduce / scan-of-sums /
+// down-sweep; neither has inter-block waits.  It can clear its input behind
+// itself, so the step's cell counters are zero for the next step.
 #include <cstdint>
 #include <cstdio>
 
@@ -70,9 +72,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int32_t* sums, int32
     }
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int32_t* __restrict__ in, int32_t n,
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int32_t* in, int32_t n,
                                                             const int32_t* __restrict__ sums,
-                                                            int32_t* __restrict__ out)
+                                                            int32_t* __restrict__ out, int32_t* clear)
 {
     int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
     int32_t v[SCAN_ITEMS], s = 0;
@@ -80,6 +82,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int32_t* __res
         v[k] = base + k < n ? in[base + k] : 0;
         s += v[k];
     }
+    if (clear)
+        for (int k = 0; k < SCAN_ITEMS; ++k)
+            if (base + k < n) clear[base + k] = 0;
     int32_t total;
     int32_t off = block_exclusive_scan(s, &total) + sums[blockIdx.x];
     for (int k = 0; k < SCAN_ITEMS; ++k) {
@@ -89,15 +94,44 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int32_t* __res
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) out[n] = off;
 }
 
+// Whole scan in one block for short inputs: thread t owns a contiguous chunk
+// of ceil(n / SCAN_THREADS) values, sums it, takes its offset from a block
+// scan of the chunk sums, then writes its chunk's prefix sums.
+constexpr int SCAN_SMALL = SCAN_THREADS * 64;
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(const int32_t* in, int32_t n,
+                                                              int32_t* __restrict__ out, int32_t* clear)
+{
+    const int per = (n + SCAN_THREADS - 1) / SCAN_THREADS;
+    const int b = threadIdx.x * per;
+    const int e = b + per < n ? b + per : n;
+    int32_t s = 0;
+    for (int k = b; k < e; ++k) s += in[k];
+    int32_t total;
+    int32_t off = block_exclusive_scan(s, &total);
+    for (int k = b; k < e; ++k) {
+        const int32_t v = in[k];
+        out[k] = off;
+        off += v;
+        if (clear) clear[k] = 0;
+    }
+    if (threadIdx.x == 0) out[n] = total;
+}
+
 int32_t scan_blocks(int64_t n) { return (int32_t)((n + SCAN_TILE - 1) / SCAN_TILE); }
 int64_t scan_max_len() { return (int64_t)SCAN_TILE * SCAN_TILE; }
 
-void scan_exclusive(const int32_t* in, int32_t n, int32_t* out, int32_t* sums, cudaStream_t st)
+int scan_exclusive(const int32_t* in, int32_t n, int32_t* out, int32_t* sums, cudaStream_t st, int32_t* clear)
 {
+    if (n <= SCAN_SMALL) {
+        k_scan_single<<<1, SCAN_THREADS, 0, st>>>(in, n, out, clear);
+        return 1;
+    }
     int nb = scan_blocks(n);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(in, n, sums);
     k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(sums, nb);
-    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(in, n, sums, out);
+    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(in, n, sums, out, clear);
+    return 3;
 }
 
 // ------------------------------------------------- stand-alone binning API
@@ -173,9 +207,9 @@ cudaError_t bin_sort_run(const double* pos, int32_t n, const double lo[3], doubl
     if (n > 0)
         k_bin_keys<<<nb, BLOCK, 0, st>>>(n, pos, lo[0], lo[1], lo[2], cs, dims[0], dims[1], dims[2],
                                          cell, id, rank, counts, n_cells);
-    scan_exclusive(counts, n_cells + 1, fullstart, sums, st);
+    scan_exclusive(counts, n_cells + 1, fullstart, sums, st, nullptr);
     if (n > 0) {
-        k_scatter<<<nb, BLOCK, 0, st>>>(n, n_cells, cell, rank, fullstart, id, tmp_src, tmp_id);
+        k_scatter<<<nb, BLOCK, 0, st>>>(n, n_cells, cell, rank, fullstart, id, tmp_src, tmp_id, nullptr);
         k_bin_order<<<nb, BLOCK, 0, st>>>(n, n_cells, fullstart, tmp_src, tmp_id, cell, key, order);
     }
     e = cudaMemcpyAsync(start, fullstart, sizeof(int32_t) * (size_t)(n_cells + 1),

@@ -28,7 +28,7 @@ EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_grid_info", "sph_get_cells", "sph_diagnostics", "sph_counters",
            "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_bin_sort_noalloc",
            "sph_profile", "sph_profile_read", "sph_tape", "sph_backward", "sph_step_async",
-           "sph_sync")
+           "sph_sync", "sph_diagnostics_async")
 SPH_ERR_CAPACITY = 8
 SPH_BIN_SORT_NOALLOC_SCRATCH = 32 << 20
 KERNEL_KINDS = ("begin_step", "predict", "scan", "scatter", "gather", "neighbors",
@@ -116,6 +116,7 @@ def lib() -> C.CDLL:
         L.sph_tape.argtypes = [p, i32, d, p]
         L.sph_step_async.argtypes = [p, i32, d]
         L.sph_sync.argtypes = [p, p]
+        L.sph_diagnostics_async.argtypes = [p, p, i32]
         L.sph_backward.argtypes = [p, p, p, i32]
         for name in EXPORTS:
             if name not in ("sph_last_error", "sph_destroy"):
@@ -255,6 +256,10 @@ def sph_sync(ctx):
     last = C.c_double(0.0)
     st = lib().sph_sync(ctx, C.byref(last))
     return st, last.value
+
+
+def sph_diagnostics_async(ctx, out_ptr: int, where: int = SPH_HOST):
+    return lib().sph_diagnostics_async(ctx, out_ptr, int(where))
 
 
 def sph_tape(ctx, nsteps: int, dt: float = 0.0):

@@ -370,3 +370,22 @@ def test_step_async_matches_step_and_reports_at_sync():
         assert sph.sph_step_async(sim.ctx, 40, 2e-4) == sph.SPH_OK
         st, _ = sph.sph_sync(sim.ctx)
         assert st == sph.SPH_ERR_DOMAIN
+
+
+def test_diagnostics_async_matches_and_checks_memory():
+    """sph_diagnostics_async into pinned host and device buffers gives the
+    values of sph_diagnostics; pageable host memory is refused."""
+    torch = pytest.importorskip("torch")
+    sc = small_dam()
+    with sph.Simulation(sc) as sim:
+        sim.step(3, 1e-4)
+        ref = sim.diagnostics()
+        pinned = torch.zeros(8, dtype=torch.float64, pin_memory=True)
+        dev = torch.zeros(8, dtype=torch.float64, device="cuda")
+        assert sph.sph_diagnostics_async(sim.ctx, pinned.data_ptr(), sph.SPH_HOST) == sph.SPH_OK
+        assert sph.sph_diagnostics_async(sim.ctx, dev.data_ptr(), sph.SPH_DEVICE) == sph.SPH_OK
+        assert sph.sph_sync(sim.ctx)[0] == sph.SPH_OK
+        assert np.array_equal(pinned.numpy(), ref)
+        assert np.array_equal(dev.cpu().numpy(), ref)
+        pageable = np.zeros(8)
+        assert sph.sph_diagnostics_async(sim.ctx, pageable.ctypes.data, sph.SPH_HOST) == sph.SPH_ERR_ARG
