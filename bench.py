@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64-form, accuracy and adjoint measurements")
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="run only the forward+backward measurement (for profiling the adjoint)")
     return ap.parse_args()
 
 
@@ -639,6 +641,13 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.adjoint_only:
+        import torch
+        from paper_2110_02621_gb300 import build
+        build.build()
+        torch.cuda.set_device(0)
+        print(json.dumps({"adjoint": adjoint_block(torch.cuda.current_stream())}), flush=True)
+        return 0
     return run_gpu(args)
 
 
