@@ -78,6 +78,21 @@ def dist_env():
     return world, rank, local
 
 
+def replica_throughput(dist, t_ms: float, particle_steps: float, device: str):
+    """Whole-job throughput of independent replicas: the particle-steps of all
+    ranks over the slowest rank's time (max over ranks), in M/s.  dist is
+    torch.distributed (any backend) or None for one process."""
+    if dist is None:
+        return particle_steps / (t_ms / 1e3) / 1e6, t_ms
+    import torch
+    t = torch.tensor([t_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([particle_steps], device=device, dtype=torch.float64)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    t_max = float(t.item())
+    return float(w.item()) / (t_max / 1e3) / 1e6, t_max
+
+
 def scene():
     from paper_2110_02621_gb300 import scenes
     return scenes.dam_break()
@@ -345,13 +360,9 @@ def run_gpu(args):
     dom_ms = prof2[dominant]["ms"] / max(prof2[dominant]["timed"], 1)
     sim.close()
 
-    if pg:
-        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_ms = float(t.item())
     parts = sc.n_fluid + active_mean
-    value = world * parts * args.steps / (t_ms / 1e3) / 1e6
-    value_fluid = world * sc.n_fluid * args.steps / (t_ms / 1e3) / 1e6
+    value, t_ms = replica_throughput(pg, t_ms, parts * args.steps, "cuda")
+    value_fluid, _ = replica_throughput(pg, t_ms, float(sc.n_fluid * args.steps), "cuda")
 
     # roofline of the dominant kernel (FP32 ALU bound: no dense contraction)
     pairs_ff = 0.5 * (ff + ff1)

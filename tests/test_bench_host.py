@@ -1,0 +1,66 @@
+"""Host logic of bench.py without a GPU: the replica aggregation over two
+gloo ranks, and the reference arm (the oracle) printing its JSON line."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    import torch.distributed as dist
+    import bench
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t_ms = [10.0, 20.0][rank]
+    q.put((rank, bench.replica_throughput(dist, t_ms, 1e6, "cpu")))
+    dist.destroy_process_group()
+
+
+def test_replica_throughput_two_gloo_ranks():
+    """value = sum of the ranks' particle-steps / the slowest rank's time."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    out = dict(q.get(timeout=120) for _ in ps)
+    for p in ps:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r in (0, 1):
+        value, t_max = out[r]
+        assert t_max == 20.0
+        assert value == pytest.approx(2e6 / 0.020 / 1e6)
+
+
+def test_single_process_throughput():
+    import bench
+    value, t = bench.replica_throughput(None, 4.0, 8e5, "cpu")
+    assert t == 4.0 and value == pytest.approx(8e5 / 0.004 / 1e6)
+
+
+def test_reference_arm_prints_its_line():
+    """bench.py --impl reference runs the oracle on the host (no GPU needed)."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "2", "--warmup", "0"], capture_output=True, text=True, timeout=600,
+                       cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["value"] > 0 and line["unit"] == "M particle-steps/s"
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0
