@@ -53,7 +53,7 @@ class _Params(C.Structure):
                 ("cfl", C.c_double), ("g", C.c_double * 3),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("n_phases", C.c_int32), ("reinit_every", C.c_int32),
-                ("phase", _Phase * 2)]
+                ("phase", _Phase * 2), ("dim", C.c_int32)]
 
 
 _lib = None
@@ -66,6 +66,8 @@ def lib():
         d, i32, i64, p = C.c_double, C.c_int32, C.c_int64, C.c_void_p
         sig = {
             "orc_W": (d, [d, d]), "orc_dWdr": (d, [d, d]),
+            "orc_W_dim": (d, [d, d, i32]), "orc_dWdr_dim": (d, [d, d, i32]),
+            "orc_lattice_sigma0_dim": (d, [d, d, i32]),
             "orc_eos_p": (d, [d, p, d, d]), "orc_eos_rho": (d, [d, p, d, d]),
             "orc_riemann": (None, [d, d, d, d, d, d, d, i32, p]),
             "orc_lattice_sigma0": (d, [d, d]),
@@ -103,17 +105,18 @@ def make_params(scene) -> _Params:
         P.g[d], P.lo[d], P.hi[d] = scene.g[d], scene.lo[d], scene.hi[d]
     P.n_phases = len(scene.phases)
     P.reinit_every = scene.reinit_every
+    P.dim = getattr(scene, "dim", 3)
     for k, ph in enumerate(scene.phases):
         P.phase[k] = make_phase(ph)
     return P
 
 
-def W(r: float, h: float) -> float:
-    return lib().orc_W(r, h)
+def W(r: float, h: float, dim: int = 3) -> float:
+    return lib().orc_W(r, h) if dim == 3 else lib().orc_W_dim(r, h, dim)
 
 
-def dWdr(r: float, h: float) -> float:
-    return lib().orc_dWdr(r, h)
+def dWdr(r: float, h: float, dim: int = 3) -> float:
+    return lib().orc_dWdr(r, h) if dim == 3 else lib().orc_dWdr_dim(r, h, dim)
 
 
 def eos_p(rho: float, phase, c0: float, gamma_tait: float = 7.0) -> float:
@@ -133,8 +136,8 @@ def riemann(rhoL, UL, pL, rhoR, UR, pR, c, limiter=True):
     return tuple(out)
 
 
-def lattice_sigma0(dp: float, h: float) -> float:
-    return lib().orc_lattice_sigma0(dp, h)
+def lattice_sigma0(dp: float, h: float, dim: int = 3) -> float:
+    return lib().orc_lattice_sigma0(dp, h) if dim == 3 else lib().orc_lattice_sigma0_dim(dp, h, dim)
 
 
 def threads() -> int:

@@ -70,32 +70,40 @@ struct orc_sim {
 };
 
 /* ---------------------------------------------------------------------- */
-/* Wendland C2 kernel in 3-D, support kappa*h with kappa = 2 (Sec. 2.3,
- * Sec. 4: h = 1.3 dx, support radius 2.6 dx).
- *   W(q) = 21/(16 pi h^3) (1 - q/2)^4 (2q + 1),  q = r/h < 2.             */
-double orc_W(double r, double h)
+/* Wendland C2 kernel, support kappa*h with kappa = 2 (Sec. 2.3, Sec. 4:
+ * h = 1.3 dx, support radius 2.6 dx).
+ *   W(q) = alpha (1 - q/2)^4 (2q + 1),  q = r/h < 2,
+ *   alpha = 21/(16 pi h^3) in 3-D, 7/(4 pi h^2) in 2-D (the 2-D tank of
+ *   Sec. 4.1).                                                            */
+static double wendland_alpha(double h, int32_t dim)
+{
+    return dim == 2 ? 7.0 / (4.0 * PI * h * h) : 21.0 / (16.0 * PI * h * h * h);
+}
+
+double orc_W_dim(double r, double h, int32_t dim)
 {
     double q = r / h;
     if (q >= 2.0) return 0.0;
-    double alpha = 21.0 / (16.0 * PI * h * h * h);
     double t = 1.0 - 0.5 * q;
-    return alpha * t * t * t * t * (2.0 * q + 1.0);
+    return wendland_alpha(h, dim) * t * t * t * t * (2.0 * q + 1.0);
 }
 
 /* dW/dr of the same kernel: -5 alpha q (1 - q/2)^3 / h. */
-double orc_dWdr(double r, double h)
+double orc_dWdr_dim(double r, double h, int32_t dim)
 {
     double q = r / h;
     if (q >= 2.0) return 0.0;
-    double alpha = 21.0 / (16.0 * PI * h * h * h);
     double t = 1.0 - 0.5 * q;
-    return -5.0 * alpha * q * t * t * t / h;
+    return -5.0 * wendland_alpha(h, dim) * q * t * t * t / h;
 }
 
+double orc_W(double r, double h) { return orc_W_dim(r, h, 3); }
+double orc_dWdr(double r, double h) { return orc_dWdr_dim(r, h, 3); }
+
 /* grad_i W_ij = dW/dr * r_ij / |r_ij|  (Eq. SPH_massConservation notation) */
-static void grad_W(const double rij[3], double r, double h, double out[3])
+static void grad_W(const double rij[3], double r, double h, int32_t dim, double out[3])
 {
-    double f = orc_dWdr(r, h) / r;
+    double f = orc_dWdr_dim(r, h, dim) / r;
     out[0] = f * rij[0];
     out[1] = f * rij[1];
     out[2] = f * rij[2];
@@ -150,18 +158,21 @@ void orc_riemann(double rhoL, double UL, double pL, double rhoR, double UR,
 
 /* sigma^0: number density sum_j W of a full cubic lattice of spacing dp,
  * self included (the "initial reference" of Eq. eqrhosum). */
-double orc_lattice_sigma0(double dp, double h)
+double orc_lattice_sigma0_dim(double dp, double h, int32_t dim)
 {
     int K = (int)ceil(2.0 * h / dp) + 1;
+    int KY = dim == 2 ? 0 : K; /* 2-D: the x-z plane of the lattice */
     double s = 0.0;
     for (int i = -K; i <= K; i++)
-        for (int j = -K; j <= K; j++)
+        for (int j = -KY; j <= KY; j++)
             for (int k = -K; k <= K; k++) {
                 double r = dp * sqrt((double)(i * i + j * j + k * k));
-                s += orc_W(r, h);
+                s += orc_W_dim(r, h, dim);
             }
     return s;
 }
+
+double orc_lattice_sigma0(double dp, double h) { return orc_lattice_sigma0_dim(dp, h, 3); }
 
 /* ---------------------------------------------------------------------- */
 /* neighbour search: cell-linked list with cells of side 2h (Sec. 3, item d) */
@@ -244,6 +255,16 @@ static int in_grid(const orc_sim* s, int64_t i)
     return s->key_f[i] != KEY_NONE;
 }
 
+/* dx^3, or dx^2 in 2-D: the volume of a particle (per unit depth in 2-D);
+ * m = rho^0 dx^dim (reading R20) */
+static double volume(const orc_sim* s)
+{
+    double d = s->P.dp;
+    return s->P.dim == 2 ? d * d : d * d * d;
+}
+
+static double W_of(const orc_sim* s, double r) { return orc_W_dim(r, s->P.h, s->P.dim); }
+
 /* ---------------------------------------------------------------------- */
 /* wall unit normals, Eq. (normalVectors): n_w = Psi/|Psi| with
  * Psi = - sum_{j in wall} (m_j/rho_j) grad_w W_wj, m_j/rho_j = dx^3.
@@ -255,8 +276,8 @@ static void normal_visit(void* vctx, int64_t j, const double rij[3], double r)
 {
     (void)j;
     normal_ctx* c = (normal_ctx*)vctx;
-    double g[3], V = c->s->P.dp * c->s->P.dp * c->s->P.dp;
-    grad_W(rij, r, c->s->P.h, g);
+    double g[3], V = volume(c->s);
+    grad_W(rij, r, c->s->P.h, c->s->P.dim, g);
     for (int d = 0; d < 3; d++) c->psi[d] -= V * g[d];
 }
 
@@ -284,7 +305,7 @@ static void wallp_visit(void* vctx, int64_t f, const double rwf[3], double r)
     wallp_ctx* c = (wallp_ctx*)vctx;
     const orc_sim* s = c->s;
     if (!in_grid(s, f)) return;
-    double W = orc_W(r, s->P.h);
+    double W = W_of(s, r);
     double w = (s->P.n_phases > 1) ? W / s->rho[f] : W;
     double gr = s->P.g[0] * rwf[0] + s->P.g[1] * rwf[1] + s->P.g[2] * rwf[2];
     c->num += (s->p[f] + s->rho[f] * gr) * w;
@@ -318,20 +339,20 @@ static void sigma_visit_f(void* vctx, int64_t j, const double rij[3], double r)
     sigma_ctx* c = (sigma_ctx*)vctx;
     if (!in_grid(c->s, j)) return;
     if (!c->all && c->s->phase[j] != c->s->phase[c->i]) return;
-    c->sum += orc_W(r, c->s->P.h);
+    c->sum += W_of(c->s, r);
 }
 
 static void sigma_visit_w(void* vctx, int64_t w, const double rij[3], double r)
 {
     (void)w; (void)rij;
     sigma_ctx* c = (sigma_ctx*)vctx;
-    c->sum += orc_W(r, c->s->P.h);
+    c->sum += W_of(c->s, r);
 }
 
 static double number_density(const orc_sim* s, int64_t i)
 {
     const orc_phase* ph = &s->P.phase[s->phase[i]];
-    sigma_ctx c = {s, i, ph->density == ORC_DENSITY_SUMMATION, orc_W(0.0, s->P.h)};
+    sigma_ctx c = {s, i, ph->density == ORC_DENSITY_SUMMATION, W_of(s, 0.0)};
     for_neighbors(s, s->x + 3 * i, s->x, s->order_f, s->start_f, sigma_visit_f, &c);
     for_neighbors(s, s->x + 3 * i, s->xw, s->order_w, s->start_w, sigma_visit_w, &c);
     return c.sum;
@@ -387,7 +408,7 @@ static void cont_term(cont_ctx* c, const double rij[3], double r, double rho_j,
     orc_riemann(rho_i, UL, p_i, rho_j, UR, p_j, s->P.c0, 1, rs);
     double Ustar = rs[0], U_bar = rs[2];
     double gw[3];
-    grad_W(rij, r, s->P.h, gw);
+    grad_W(rij, r, s->P.h, s->P.dim, gw);
     double dot = 0.0;
     for (int d = 0; d < 3; d++) {
         double vmix = (rho_i * v_i[d] + rho_j * v_j[d]) / (rho_i + rho_j);
@@ -402,7 +423,7 @@ static void cont_visit_f(void* vctx, int64_t j, const double rij[3], double r)
     cont_ctx* c = (cont_ctx*)vctx;
     const orc_sim* s = c->s;
     if (!in_grid(s, j)) return;
-    double m_j = s->P.phase[s->phase[j]].rho0 * s->P.dp * s->P.dp * s->P.dp;
+    double m_j = s->P.phase[s->phase[j]].rho0 * volume(s);
     cont_term(c, rij, r, s->rho[j], s->p[j], c->vel + 3 * j, m_j);
 }
 
@@ -411,7 +432,7 @@ static void cont_visit_w(void* vctx, int64_t w, const double rij[3], double r)
     cont_ctx* c = (cont_ctx*)vctx;
     const orc_sim* s = c->s;
     int ph = s->phase[c->i];
-    double m_w = s->P.phase[ph].rho0 * s->P.dp * s->P.dp * s->P.dp;
+    double m_w = s->P.phase[ph].rho0 * volume(s);
     double zero[3] = {0.0, 0.0, 0.0};
     cont_term(c, rij, r, s->rhow[2 * w + ph], s->pw[w], zero, m_w);
 }
@@ -433,21 +454,21 @@ static void sum_visit_f(void* vctx, int64_t j, const double rij[3], double r)
     (void)rij;
     sum_ctx* c = (sum_ctx*)vctx;
     if (!in_grid(c->s, j)) return;
-    c->sum += orc_W(r, c->s->P.h);
+    c->sum += W_of(c->s, r);
 }
 
 static void sum_visit_w(void* vctx, int64_t w, const double rij[3], double r)
 {
     (void)w; (void)rij;
     sum_ctx* c = (sum_ctx*)vctx;
-    c->sum += orc_W(r, c->s->P.h);
+    c->sum += W_of(c->s, r);
 }
 
 static double summation_density(const orc_sim* s, int64_t i)
 {
     const orc_phase* ph = &s->P.phase[s->phase[i]];
-    double m_i = ph->rho0 * s->P.dp * s->P.dp * s->P.dp;
-    sum_ctx c = {s, orc_W(0.0, s->P.h)};
+    double m_i = ph->rho0 * volume(s);
+    sum_ctx c = {s, W_of(s, 0.0)};
     for_neighbors(s, s->x + 3 * i, s->x, s->order_f, s->start_f, sum_visit_f, &c);
     for_neighbors(s, s->x + 3 * i, s->xw, s->order_w, s->start_w, sum_visit_w, &c);
     return m_i * c.sum;
@@ -475,7 +496,7 @@ static void viscous_term(mom_ctx* c, const double rij[3], double r, double rho_j
     double mu_i = s->P.phase[s->phase[i]].mu;
     if (mu_i + mu_j == 0.0) return;
     double gw[3];
-    grad_W(rij, r, s->P.h, gw);
+    grad_W(rij, r, s->P.h, s->P.dim, gw);
     double rg = rij[0] * gw[0] + rij[1] * gw[1] + rij[2] * gw[2];
     double k = m_j * (mu_i + mu_j) * rg /
                (s->rho[i] * rho_j * (r * r + 0.01 * s->P.h * s->P.h));
@@ -496,9 +517,9 @@ static void mom_visit_f(void* vctx, int64_t j, const double rij[3], double r)
     orc_riemann(s->rho[i], UL, s->p[i], s->rho[j], UR, s->p[j], s->P.c0, 1, rs);
     double pstar = rs[1];
     const orc_phase* phj = &s->P.phase[s->phase[j]];
-    double m_j = phj->rho0 * s->P.dp * s->P.dp * s->P.dp;
+    double m_j = phj->rho0 * volume(s);
     double gw[3];
-    grad_W(rij, r, s->P.h, gw);
+    grad_W(rij, r, s->P.h, s->P.dim, gw);
     for (int d = 0; d < 3; d++) c->a[d] += -2.0 * m_j * pstar / (s->rho[i] * s->rho[j]) * gw[d];
     viscous_term(c, rij, r, s->rho[j], phj->mu, v_j, m_j);
 }
@@ -512,11 +533,11 @@ static void mom_visit_w(void* vctx, int64_t w, const double rij[3], double r)
     const orc_phase* phi = &s->P.phase[ph];
     double rho_i = s->rho[i], p_i = s->p[i];
     double rho_w = s->rhow[2 * w + ph], p_w = s->pw[w];
-    double m_w = phi->rho0 * s->P.dp * s->P.dp * s->P.dp;
+    double m_w = phi->rho0 * volume(s);
     /* Eq. (RSatWall) */
     double pstar = (rho_i * p_w + rho_w * p_i) / (rho_i + rho_w);
     double gw[3];
-    grad_W(rij, r, s->P.h, gw);
+    grad_W(rij, r, s->P.h, s->P.dim, gw);
     for (int d = 0; d < 3; d++) c->a[d] += -2.0 * m_w * pstar / (rho_i * rho_w) * gw[d];
     double zero[3] = {0.0, 0.0, 0.0};
     viscous_term(c, rij, r, rho_w, phi->mu, zero, m_w);
@@ -529,7 +550,7 @@ static void mom_visit_w(void* vctx, int64_t w, const double rij[3], double r)
         double lambda = (delta < 1.0) ? (1.0 - delta) * (1.0 - delta) / dx : 0.0;
         double Ppen = s->P.gamma_p * lambda * fabs(p_i * en);
         double k = -2.0 * m_w / (rho_i * rho_w) * Ppen * (dx * dx * dx) / (r * r) *
-                   orc_dWdr(r, s->P.h);
+                   orc_dWdr_dim(r, s->P.h, s->P.dim);
         for (int d = 0; d < 3; d++) c->a[d] += k * n_w[d];
     }
 }
@@ -648,6 +669,7 @@ orc_sim* orc_create(const orc_params* P, int64_t nf, const double* x,
 {
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
     s->P = *P;
+    if (s->P.dim != 2) s->P.dim = 3;
     s->nf = nf;
     s->nw = nw;
     s->cs = 2.0 * P->h;
@@ -689,7 +711,7 @@ orc_sim* orc_create(const orc_params* P, int64_t nf, const double* x,
                                      P->c0, P->gamma_tait);
         s->p[i] = orc_eos_p(s->rho[i], ph, P->c0, P->gamma_tait);
     }
-    s->sigma0 = orc_lattice_sigma0(P->dp, P->h);
+    s->sigma0 = orc_lattice_sigma0_dim(P->dp, P->h, s->P.dim);
     wall_pressure(s);
     momentum(s, s->v);
     compute_sigma(s);
@@ -797,9 +819,9 @@ void orc_diagnostics(const orc_sim* s, double out[8])
 {
     double m_tot = 0, px = 0, py = 0, pz = 0, ek = 0, ep = 0;
     int64_t esc = 0;
-    double dp3 = s->P.dp * s->P.dp * s->P.dp;
+    double vol = volume(s);
     for (int64_t i = 0; i < s->nf; i++) {
-        double m = s->P.phase[s->phase[i]].rho0 * dp3;
+        double m = s->P.phase[s->phase[i]].rho0 * vol;
         const double *v = s->v + 3 * i, *x = s->x + 3 * i;
         m_tot += m;
         px += m * v[0];

@@ -49,13 +49,18 @@ typedef struct {
     int32_t n_phases;
     int32_t reinit_every; /* reinitialise at steps n with n % k == 0; 0 = never */
     orc_phase phase[2];
+    int32_t dim;          /* 3, or 2: particles in one x-z plane (all y equal) */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
 
-/* kernel and equation of state, exposed for the pins */
+/* kernel and equation of state, exposed for the pins (orc_W, orc_dWdr and
+ * orc_lattice_sigma0: 3-D; the _dim forms take dim = 2 or 3) */
 double orc_W(double r, double h);
 double orc_dWdr(double r, double h);
+double orc_W_dim(double r, double h, int32_t dim);
+double orc_dWdr_dim(double r, double h, int32_t dim);
+double orc_lattice_sigma0_dim(double dp, double h, int32_t dim);
 double orc_eos_p(double rho, const orc_phase* ph, double c0, double gamma_tait);
 double orc_eos_rho(double p, const orc_phase* ph, double c0, double gamma_tait);
 void orc_riemann(double rhoL, double UL, double pL, double rhoR, double UR,

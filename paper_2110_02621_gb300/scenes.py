@@ -64,6 +64,7 @@ class Scene:
     steps: int = 1
     probes: Optional[np.ndarray] = None   # indices into wall_pos
     rho_init: Optional[np.ndarray] = None  # None: hydrostatic initial density
+    dim: int = 3                           # 2: particles in the x-z plane y = 0
 
     @property
     def n_fluid(self) -> int:
@@ -311,6 +312,83 @@ def jittered_blob(n: Tuple[int, int, int] = (16, 16, 16), dp: float = 0.01,
         sc.rho_init = 1000.0 * (1.0 + rng.uniform(-rho_jitter, rho_jitter,
                                                   size=pos.shape[0]))
     return sc
+
+
+# ------------------------------------------------------------------ 2-D
+def lattice2d(n: Tuple[int, int], dp: float,
+              origin: Tuple[float, float] = (0.0, 0.0)) -> np.ndarray:
+    """(k + 1/2) dp sites of an nx x nz block in the plane y = 0."""
+    nx, nz = n
+    z, x = np.meshgrid(np.arange(nz), np.arange(nx), indexing="ij")
+    pts = np.stack([(x.ravel() + 0.5) * dp + origin[0], np.zeros(x.size),
+                    (z.ravel() + 0.5) * dp + origin[1]], axis=1)
+    return pts.astype(np.float64)
+
+
+def box_walls2d(inner: Tuple[int, int], dp: float, layers: int = 3, roof: bool = True) -> np.ndarray:
+    """Wall dummy particles filling ``layers`` lattice layers outside an
+    inner box of nx x nz sites (floor and side walls, and a roof if asked)."""
+    nx, nz = inner
+    top = nz + layers if roof else nz
+    kx = np.arange(-layers, nx + layers)
+    kz = np.arange(-layers, top)
+    z, x = np.meshgrid(kz, kx, indexing="ij")
+    x, z = x.ravel(), z.ravel()
+    inside = (x >= 0) & (x < nx) & (z >= 0) & ((z < nz) if roof else True)
+    pts = np.stack([(x[~inside] + 0.5) * dp, np.zeros((~inside).sum()), (z[~inside] + 0.5) * dp], axis=1)
+    return pts.astype(np.float64)
+
+
+def _domain2d(wall: np.ndarray, fluid: np.ndarray, cell: float, head: float):
+    allp = np.concatenate([wall, fluid], axis=0)
+    lo = (float(allp[:, 0].min() - cell), -0.5 * cell, float(allp[:, 2].min() - cell))
+    hi = (float(allp[:, 0].max() + cell), 0.5 * cell, float(allp[:, 2].max() + cell + head))
+    return lo, hi
+
+
+def two_phase_hydrostatic_tank_2d(dx: float = 0.01, L: float = 1.0, H: float = 0.5,
+                                  layers: int = 3) -> Scene:
+    """The 2-D two-phase hydrostatic tank of Sec. 4.1: a closed tank of length
+    L = 2H = 1 m and height 2H, water (rho0 = 1000) in the lower half, air
+    (rho0 = 1) in the upper half, both at rest; particle spacing dx (the
+    paper uses 0.01, 0.005, 0.0025, 0.00125 m).  Both fluids inviscid, linear
+    EOS with one c0 = 10 sqrt(g H); air with summation density and the
+    penalty force, as in the 3-D two-phase case."""
+    nx, nz = _count(L, dx), _count(2 * H, dx)
+    h = 1.3 * dx
+    fluid = lattice2d((nx, nz), dx)
+    phase = np.where(fluid[:, 2] < H, 0, 1).astype(np.int32)
+    wall = box_walls2d((nx, nz), dx, layers, roof=True)
+    lo, hi = _domain2d(wall, fluid, 2 * h, 0.0)
+    return Scene(
+        name=f"two_phase_hydrostatic_tank_2d_dx{dx:g}", dp=dx, h=h,
+        c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G), lo=lo, hi=hi,
+        phases=[Phase(rho0=1000.0, eos="linear", density="continuity",
+                      reinit="free_surface", penalty=False, z_top=H),
+                Phase(rho0=1.0, eos="linear", density="summation",
+                      reinit="internal", penalty=True, z_top=2 * H)],
+        fluid_pos=fluid, fluid_vel=np.zeros_like(fluid), fluid_phase=phase,
+        wall_pos=wall, reinit_every=1, steps=1, dim=2)
+
+
+def dam_break_2d(tank: Tuple[float, float] = (0.4, 0.3), column: Tuple[float, float] = (0.15, 0.15),
+                 dx: float = 0.005, layers: int = 3, penalty: bool = True, reinit_every: int = 20) -> Scene:
+    """A 2-D dam break in the x-z plane: a water column at x = 0 in an open
+    tank (Tait EOS, penalty on, reinitialisation every 20 steps)."""
+    ntx, ntz = _count(tank[0], dx), _count(tank[1], dx)
+    ncx, ncz = _count(column[0], dx), _count(column[1], dx)
+    h = 1.3 * dx
+    H = ncz * dx
+    fluid = lattice2d((ncx, ncz), dx)
+    wall = box_walls2d((ntx, ntz), dx, layers, roof=False)
+    lo, hi = _domain2d(wall, fluid, 2 * h, 0.25 * tank[1])
+    return Scene(
+        name=f"dam_break_2d_{tank[0]:g}x{tank[1]:g}_dx{dx:g}", dp=dx, h=h,
+        c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G), lo=lo, hi=hi,
+        phases=[Phase(rho0=1000.0, eos="tait", penalty=penalty, z_top=H)],
+        fluid_pos=fluid, fluid_vel=np.zeros_like(fluid),
+        fluid_phase=np.zeros(fluid.shape[0], np.int32), wall_pos=wall,
+        reinit_every=reinit_every, steps=1, dim=2)
 
 
 def perturbed(sc: Scene, jitter: float = 0.3, shift: Tuple[float, float, float] = (0.0, 0.0, 0.0),
