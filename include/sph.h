@@ -91,7 +91,10 @@ typedef struct {
     int32_t precision;  /* SPH_FP32: FP32 pair arithmetic, positions as cell  *
                          * index + FP32 offset with Kahan-compensated drift;  *
                          * SPH_FP64_PLAIN: the same kernels in FP64           */
-    int32_t reserved;   /* must be 0                                          */
+    int32_t dim;        /* 3 (or 0): 3-D.  2: the 2-D form (Sec. 4.1): every  *
+                         * fluid and wall particle in one plane y = const    *
+                         * (checked), Wendland C2 with 7/(4 pi h^2), masses  *
+                         * rho0 dx^2 per unit depth                          */
 } sph_params;
 
 /* Fluid particles.  rho may be NULL: each particle then starts from the

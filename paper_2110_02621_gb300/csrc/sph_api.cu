@@ -38,7 +38,7 @@ sph_status validate(const sph_params* P, const sph_fluid* F, const sph_wall* W, 
     if (P->n_phases < 1 || P->n_phases > 2) return bad(msg, "n_phases must be 1 or 2");
     if (P->reinit_every < 0) return bad(msg, "reinit_every must be >= 0");
     if (P->precision != SPH_FP32 && P->precision != SPH_FP64_PLAIN) return bad(msg, "unknown precision");
-    if (P->reserved != 0) return bad(msg, "reserved must be 0");
+    if (P->dim != 0 && P->dim != 2 && P->dim != 3) return bad(msg, "dim must be 0, 2 or 3");
     for (int k = 0; k < P->n_phases; ++k) {
         const sph_phase& ph = P->phase[k];
         if (!(ph.rho0 > 0) || !(ph.mu >= 0) || !std::isfinite(ph.rho0 + ph.mu + ph.z_top))
@@ -66,6 +66,16 @@ sph_status validate(const sph_params* P, const sph_fluid* F, const sph_wall* W, 
     }
     for (int64_t i = 0; i < nw; ++i)
         if (!finite3(W->pos + 3 * i)) return bad(msg, "non-finite wall position");
+    if (P->dim == 2) {
+        // one plane: every y equal (pairs then have r_y = 0 exactly)
+        const double y0 = F->n > 0 ? F->pos[1] : (nw > 0 ? W->pos[1] : 0.0);
+        for (int64_t i = 0; i < F->n; ++i)
+            if (F->pos[3 * i + 1] != y0 || (F->vel && F->vel[3 * i + 1] != 0.0))
+                return bad(msg, "dim = 2: every particle needs the same y and zero y velocity");
+        for (int64_t i = 0; i < nw; ++i)
+            if (W->pos[3 * i + 1] != y0) return bad(msg, "dim = 2: every particle needs the same y");
+        if (P->g[1] != 0.0) return bad(msg, "dim = 2: g must lie in the x-z plane");
+    }
     return SPH_OK;
 }
 

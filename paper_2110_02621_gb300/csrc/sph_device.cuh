@@ -39,10 +39,11 @@ struct Cfg {
     T inv_h;
     T c0, inv_c0, gamma, inv_gamma, gamma_p;
     T dp, dp3, inv_dp, eta2, pen_rmin;  // dx, dx^3, 1/dx, 0.01 h^2, 1e-6 dx
+    T vol;                  // particle volume dx^3 (3-D) or dx^2 (2-D, per unit depth)
     T gx, gy, gz;
     T inv_sigma0;           // 1 / (lattice number density)
     T sigma0_hi, sigma0_lo; // lattice number density sigma^0 as an unevaluated sum
-    T inv_dp3_hi, inv_dp3_lo;  // 1/dx^3 likewise (summation-density reference)
+    T inv_vol_hi, inv_vol_lo;  // 1/vol likewise (summation-density reference)
     T cfl, body_dt;         // cfl, cfl*sqrt(h/|g|) (0 if g = 0)
     int32_t nx, ny, nz, n_cells;
     int32_t n_phases;

@@ -154,9 +154,9 @@ __global__ void k_wall_normals(Cfg<double> D, int32_t n, const int32_t* __restri
             double r2 = rx * rx + ry * ry + rz * rz;
             if (r2 >= D.rc2 || r2 == 0.0) return;
             double F = kernel_F(D, sqrt(r2));
-            px -= D.dp3 * F * rx;
-            py -= D.dp3 * F * ry;
-            pz -= D.dp3 * F * rz;
+            px -= D.vol * F * rx;
+            py -= D.vol * F * ry;
+            pz -= D.vol * F * rz;
         });
     }
     double m = sqrt(px * px + py * py + pz * pz);

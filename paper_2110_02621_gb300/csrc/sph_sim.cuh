@@ -44,14 +44,22 @@ namespace sph {
 inline int grid_for(int64_t n) { return (int)((n + BLOCK - 1) / BLOCK); }
 
 
-// number density of a full cubic lattice of spacing dp, self included
-inline double lattice_sigma0(double dp, double h)
+// Wendland C2 normalisation: 21/(16 pi h^3) in 3-D, 7/(4 pi h^2) in 2-D
+inline double wendland_alpha(double h, int dim)
+{
+    const double pi = 3.14159265358979323846;
+    return dim == 2 ? 7.0 / (4.0 * pi * h * h) : 21.0 / (16.0 * pi * h * h * h);
+}
+
+// number density of a full lattice of spacing dp (cubic, or square in the
+// x-z plane in 2-D), self included
+inline double lattice_sigma0(double dp, double h, int dim)
 {
     int K = (int)std::ceil(2.0 * h / dp) + 1;
-    const double pi = 3.14159265358979323846;
-    double alpha = 21.0 / (16.0 * pi * h * h * h), s = 0.0;
+    const int KY = dim == 2 ? 0 : K;
+    double alpha = wendland_alpha(h, dim), s = 0.0;
     for (int i = -K; i <= K; ++i)
-        for (int j = -K; j <= K; ++j)
+        for (int j = -KY; j <= KY; ++j)
             for (int k = -K; k <= K; ++k) {
                 double q = dp * std::sqrt((double)(i * i + j * j + k * k)) / h;
                 if (q < 2.0) {
@@ -65,10 +73,11 @@ inline double lattice_sigma0(double dp, double h)
 template <class T>
 Cfg<T> make_cfg(const sph_params& P, const int32_t dims[3])
 {
-    const double pi = 3.14159265358979323846;
     Cfg<T> C;
     double h = P.h, cs = 2.0 * h;
-    double alpha = 21.0 / (16.0 * pi * h * h * h);
+    const int dim = P.dim == 2 ? 2 : 3;
+    const double vol = dim == 2 ? P.dp * P.dp : P.dp * P.dp * P.dp;  // particle volume dx^dim
+    double alpha = wendland_alpha(h, dim);
     C.h = (T)h;
     C.rc2 = (T)(cs * cs);
     C.cs = (T)cs;
@@ -82,19 +91,20 @@ Cfg<T> make_cfg(const sph_params& P, const int32_t dims[3])
     C.inv_gamma = (T)(1.0 / P.gamma_tait);
     C.gamma_p = (T)P.gamma_p;
     C.dp = (T)P.dp;
-    C.dp3 = (T)(P.dp * P.dp * P.dp);
+    C.dp3 = (T)(P.dp * P.dp * P.dp);  // the penalty's dx^3 (in 2-D as well)
+    C.vol = (T)vol;
     C.inv_dp = (T)(1.0 / P.dp);
     C.eta2 = (T)(0.01 * h * h);
     C.pen_rmin = (T)(1e-6 * P.dp);
     C.gx = (T)P.g[0];
     C.gy = (T)P.g[1];
     C.gz = (T)P.g[2];
-    const double sigma0 = lattice_sigma0(P.dp, h), inv_dp3 = 1.0 / (P.dp * P.dp * P.dp);
+    const double sigma0 = lattice_sigma0(P.dp, h, dim), inv_vol = 1.0 / vol;
     C.inv_sigma0 = (T)(1.0 / sigma0);
     C.sigma0_hi = (T)sigma0;
     C.sigma0_lo = (T)(sigma0 - (double)C.sigma0_hi);
-    C.inv_dp3_hi = (T)inv_dp3;
-    C.inv_dp3_lo = (T)(inv_dp3 - (double)C.inv_dp3_hi);
+    C.inv_vol_hi = (T)inv_vol;
+    C.inv_vol_lo = (T)(inv_vol - (double)C.inv_vol_hi);
     C.cfl = (T)P.cfl;
     double gn = std::sqrt(P.g[0] * P.g[0] + P.g[1] * P.g[1] + P.g[2] * P.g[2]);
     C.body_dt = gn > 0.0 ? (T)(P.cfl * std::sqrt(h / gn)) : T(0);
@@ -109,7 +119,7 @@ Cfg<T> make_cfg(const sph_params& P, const int32_t dims[3])
         q.rho0 = (T)ph.rho0;
         q.inv_rho0 = (T)(1.0 / ph.rho0);
         q.mu = (T)ph.mu;
-        q.m = (T)(ph.rho0 * P.dp * P.dp * P.dp);
+        q.m = (T)(ph.rho0 * vol);
         q.eos_k = ph.eos == SPH_EOS_TAIT ? (T)(ph.rho0 * P.c0 * P.c0 / P.gamma_tait) : (T)(P.c0 * P.c0);
         q.eos = ph.eos;
         q.density = ph.density;
@@ -157,7 +167,7 @@ class Sim final : public SimBase {
         I_.gamma = P.gamma_tait;
         I_.n_phases = P.n_phases;
         I_.has_rho = F.rho != nullptr;
-        I_.sigma0 = lattice_sigma0(P.dp, P.h);
+        I_.sigma0 = lattice_sigma0(P.dp, P.h, P.dim == 2 ? 2 : 3);
         for (int k = 0; k < 2; ++k) {
             const sph_phase& ph = P.phase[k < P.n_phases ? k : 0];
             I_.rho0[k] = ph.rho0;

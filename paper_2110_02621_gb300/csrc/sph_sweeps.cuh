@@ -308,7 +308,8 @@ __device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t,
 // (rho_w, p_w) and m_w = m_i.  Then rho^{n+1} = rho^n + dt d rho/dt (Sec. 2.6).
 // Light (summation) phases: Eq. (densitySummation), rho = m sum_j W_ij over
 // all particles and walls, self included, evaluated as
-// rho - rho0 = rho0 dx^3 (sum_j W_ij - 1/dx^3) with a compensated sum.  The
+// rho - rho0 = rho0 vol (sum_j W_ij - 1/vol), vol = dx^3 (dx^2 in 2-D), with a
+// compensated sum.  The
 // EOS then gives p^{n+1}.  Particles outside the grid keep their state and
 // get a = 0 (their momentum outputs are written here: nobody reads them).
 template <class T>
@@ -349,7 +350,7 @@ __global__ void __launch_bounds__(LBLOCK) k_continuity(
                       [&](int, const V4<T>&, T, T, T, T r2) { kahan_add(s, e, kernel_W(C, r2 * p_rsqrt(r2))); },
                       [&](int, const V4<T>&, T, T, T, T r2) { kahan_add(s, e, kernel_W(C, r2 * p_rsqrt(r2))); });
         group_kahan(s, e);
-        d = P.rho0 * C.dp3 * minus_ref(s, e, C.inv_dp3_hi, C.inv_dp3_lo);
+        d = P.rho0 * C.vol * minus_ref(s, e, C.inv_vol_hi, C.inv_vol_lo);
     } else {
         T s = T(0);
         const T kc = C.inv_c0;

@@ -48,7 +48,7 @@ class sph_params(C.Structure):
                 ("gamma_tait", C.c_double), ("gamma_p", C.c_double), ("cfl", C.c_double),
                 ("g", C.c_double * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("n_phases", C.c_int32), ("reinit_every", C.c_int32),
-                ("phase", sph_phase * 2), ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("phase", sph_phase * 2), ("precision", C.c_int32), ("dim", C.c_int32)]
 
 
 class sph_fluid(C.Structure):
@@ -148,7 +148,7 @@ def make_params(scene, precision: int = SPH_FP32) -> sph_params:
                                density=_DENSITY[ph.density], reinit=_REINIT[ph.reinit],
                                penalty=int(bool(ph.penalty)))
     P.precision = precision
-    P.reserved = 0
+    P.dim = getattr(scene, "dim", 3)
     return P
 
 

@@ -58,6 +58,19 @@ def check_cells(sim, ref, n_in_only=False):
     assert np.array_equal(g["start_w"], o["start_w"].astype(np.int32))
 
 
+def heavy_floor(sc, o):
+    """FP32 floor of a continuity (heavy) phase acceleration in deep water:
+    the pressure-gradient sum adds pair terms of size ~ 2 p / (rho0 h) that
+    cancel down to O(g), so FP32 rounding of the terms (2^-24 relative) leaves
+    ~ c 2^-24 2 p_max / (rho0 h) with c ~ 5 (measured, 2-D tank at dx = 0.02
+    and 0.01); bound with c = 16.  Below the 2e-5 |g| tolerance for the
+    benchmark's dam break (H = 23 h); above it for the deep 2-D tank (H = 38 h)."""
+    heavy = [k for k, ph in enumerate(sc.phases) if ph.density == "continuity"]
+    sel = np.isin(sc.fluid_phase, heavy)
+    rho0 = max(sc.phases[k].rho0 for k in heavy)
+    return 16.0 * 2.0 ** -24 * 2.0 * float(np.abs(o["p"][sel]).max()) / (rho0 * sc.h)
+
+
 def light_floor(sc):
     """FP32 floor of a summation-density (light) phase acceleration.  Its
     density is m sum_j W_ij, so the FP32 rounding of the positions
@@ -68,11 +81,15 @@ def light_floor(sc):
 
 
 def check_state(g, o, ow, dp, tol_rate=TOL_RATE, tol_x=TOL_X, what="", gnorm=9.81, light=None,
-                floor=0.0):
+                floor=0.0, heavy_abs=None):
     assert np.abs(g["x"] - o["x"]).max() <= tol_x * dp, what
     heavy = np.ones(len(o["a"]), bool) if light is None else ~light
-    ea = rel_inf(g["a"][heavy], o["a"][heavy], gnorm)
-    assert ea <= tol_rate, (what, ea)
+    if heavy_abs is not None:
+        eh = np.abs(g["a"][heavy] - o["a"][heavy]).max()
+        assert eh <= max(tol_rate * max(np.abs(o["a"][heavy]).max(), gnorm), heavy_abs), (what, eh, heavy_abs)
+    else:
+        ea = rel_inf(g["a"][heavy], o["a"][heavy], gnorm)
+        assert ea <= tol_rate, (what, ea)
     if light is not None and light.any():
         el = np.abs(g["a"][light] - o["a"][light]).max()
         assert el <= max(tol_rate * max(np.abs(o["a"]).max(), gnorm), floor), (what, el, floor)
@@ -389,3 +406,52 @@ def test_diagnostics_async_matches_and_checks_memory():
         assert np.array_equal(dev.cpu().numpy(), ref)
         pageable = np.zeros(8)
         assert sph.sph_diagnostics_async(sim.ctx, pageable.ctypes.data, sph.SPH_HOST) == sph.SPH_ERR_ARG
+
+
+# --------------------------------------------------------------------- 2-D
+@pytest.mark.parametrize("make,tol", [(lambda: S.two_phase_hydrostatic_tank_2d(dx=0.02), 5e-5),
+                                      (lambda: S.dam_break_2d(dx=0.01), TOL_RATE)],
+                         ids=["two_phase_tank_2d", "dam_break_2d"])
+def test_2d_parity(make, tol):
+    """The 2-D form (Sec. 4.1): cells bit-exact, created state and one CFL
+    step within the single-step tolerance, then trajectories and densities
+    after 20 more steps; FP64 plain form to round-off.  In the two-phase
+    tank the water next to the air inherits the air's FP32 pressure floor
+    (its density is a summation, see light_floor) through pressure
+    differences of only rho_a g r ~ 0.2 Pa across the interface: measured
+    2.2e-5 of the largest d rho/dt, bounded here by 5e-5."""
+    sc = make()
+    ref = oracle.OracleSim(sc)
+    light = np.array([sc.phases[p].density == "summation" for p in range(len(sc.phases))])[sc.fluid_phase]
+    with sph.Simulation(sc) as sim:
+        check_cells(sim, ref)
+        o = ref.fluid()
+        check_state(sim.state(), o, ref.wall(), sc.dp, tol_rate=tol, what="create", light=light,
+                    floor=light_floor(sc), heavy_abs=heavy_floor(sc, o))
+        dt = sim.step(1)
+        assert abs(dt - ref.step(1)) <= 1e-6 * dt
+        g, o = sim.state(), ref.fluid()
+        check_state(g, o, ref.wall(), sc.dp, tol_rate=tol, what="first step", light=light,
+                    floor=light_floor(sc), heavy_abs=heavy_floor(sc, o))
+        # one plane: every y the same (the FP32 offset of y0 from its cell's corner)
+        assert np.ptp(g["x"][:, 1]) == 0.0 and abs(g["x"][0, 1] - sc.fluid_pos[0, 1]) < 1e-9
+        assert np.all(g["a"][:, 1] == 0.0) and np.all(g["v"][:, 1] == 0.0)
+        sim.step(20)
+        ref.step(20)
+        g, o = sim.state(), ref.fluid()
+        assert np.abs(g["x"] - o["x"]).max() <= TOL_X * sc.dp
+        assert rel_inf(g["rho"], o["rho"]) <= 1e-5
+    ref2 = oracle.OracleSim(sc)
+    with sph.Simulation(sc, precision=sph.SPH_FP64_PLAIN) as sim:
+        sim.step(5, 1e-4)
+        ref2.step(5, 1e-4)
+        check_state(sim.state(), ref2.fluid(), ref2.wall(), sc.dp, tol_rate=1e-7, tol_x=1e-9, what="fp64")
+
+
+def test_2d_input_checks():
+    sc = S.dam_break_2d(dx=0.01)
+    sc.fluid_pos = sc.fluid_pos.copy()
+    sc.fluid_pos[3, 1] = 1e-3
+    with pytest.raises(sph.SphError) as e:
+        sph.Simulation(sc)
+    assert e.value.status == sph.SPH_ERR_ARG
