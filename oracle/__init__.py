@@ -79,6 +79,7 @@ def lib():
             "orc_neighbors": (i64, [p, i64, p, i64, p, p, i64, p]),
             "orc_diagnostics": (None, [p, p]), "orc_sigma0": (d, [p]),
             "orc_step_count": (i64, [p]), "orc_threads": (i32, []),
+            "orc_set_excitation": (None, [p, p, d]), "orc_time": (d, [p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -180,6 +181,15 @@ class OracleSim:
 
     def reinit_density(self):
         lib().orc_reinit_density(self._h)
+
+    def set_excitation(self, amp, freq: float):
+        """Rigid sinusoidal tank motion x = amp sin(2 pi freq t), in the tank frame."""
+        a = np.ascontiguousarray(amp, np.float64)
+        lib().orc_set_excitation(self._h, _ptr(a), float(freq))
+
+    @property
+    def time(self) -> float:
+        return lib().orc_time(self._h)
 
     def rates(self):
         drho = np.zeros(self.nf)

@@ -67,7 +67,17 @@ struct orc_sim {
     double sigma0;
     int64_t step;
     double last_dt;
+    /* rigid sinusoidal tank motion x_w = amp sin(2 pi f t) (Sec. 4.2),
+     * simulated in the tank's frame: the body force there is
+     * g_eff = g - d2x/dt2 = g + amp (2 pi f)^2 sin(2 pi f t) */
+    double t, ex_amp[3], ex_freq, geff[3];
 };
+
+static void body_force(orc_sim* s, double t)
+{
+    double w = 2.0 * PI * s->ex_freq, sw = sin(w * t);
+    for (int d = 0; d < 3; d++) s->geff[d] = s->P.g[d] + s->ex_amp[d] * w * w * sw;
+}
 
 /* ---------------------------------------------------------------------- */
 /* Wendland C2 kernel, support kappa*h with kappa = 2 (Sec. 2.3, Sec. 4:
@@ -307,7 +317,7 @@ static void wallp_visit(void* vctx, int64_t f, const double rwf[3], double r)
     if (!in_grid(s, f)) return;
     double W = W_of(s, r);
     double w = (s->P.n_phases > 1) ? W / s->rho[f] : W;
-    double gr = s->P.g[0] * rwf[0] + s->P.g[1] * rwf[1] + s->P.g[2] * rwf[2];
+    double gr = s->geff[0] * rwf[0] + s->geff[1] * rwf[1] + s->geff[2] * rwf[2];
     c->num += (s->p[f] + s->rho[f] * gr) * w;
     c->den += w;
 }
@@ -560,7 +570,7 @@ static void acceleration(const orc_sim* s, int64_t i, const double* vel, double 
     mom_ctx c = {s, i, vel, {0.0, 0.0, 0.0}};
     for_neighbors(s, s->x + 3 * i, s->x, s->order_f, s->start_f, mom_visit_f, &c);
     for_neighbors(s, s->x + 3 * i, s->xw, s->order_w, s->start_w, mom_visit_w, &c);
-    for (int d = 0; d < 3; d++) out[d] = c.a[d] + s->P.g[d];
+    for (int d = 0; d < 3; d++) out[d] = c.a[d] + s->geff[d];
 }
 
 static void momentum(orc_sim* s, const double* vel)
@@ -592,7 +602,10 @@ static double max_speed(const orc_sim* s)
 static double time_step(const orc_sim* s)
 {
     double dt = s->P.cfl * s->P.h / (s->P.c0 + max_speed(s));
+    /* body-force limit with the largest |g_eff| of the motion, |g| + |amp| w^2 */
     double gn = sqrt(s->P.g[0] * s->P.g[0] + s->P.g[1] * s->P.g[1] + s->P.g[2] * s->P.g[2]);
+    double w = 2.0 * PI * s->ex_freq;
+    gn += sqrt(s->ex_amp[0] * s->ex_amp[0] + s->ex_amp[1] * s->ex_amp[1] + s->ex_amp[2] * s->ex_amp[2]) * w * w;
     if (gn > 0.0) dt = fmin(dt, s->P.cfl * sqrt(s->P.h / gn));
     return dt;
 }
@@ -631,7 +644,10 @@ static double one_step(orc_sim* s, double dt_in)
         s->p[i] = orc_eos_p(s->rho[i], &s->P.phase[s->phase[i]], s->P.c0, s->P.gamma_tait);
     }
     free(rho_new);
-    /* wall pressure from the updated fluid, then momentum at n+1 */
+    /* the body force of t^{n+1}, then wall pressure from the updated fluid
+     * and momentum at n+1 */
+    s->t += dt;
+    body_force(s, s->t);
     wall_pressure(s);
     momentum(s, s->v);
     /* v^{n+1} = v^{n+1/2} + dt/2 a^{n+1} */
@@ -670,6 +686,7 @@ orc_sim* orc_create(const orc_params* P, int64_t nf, const double* x,
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
     s->P = *P;
     if (s->P.dim != 2) s->P.dim = 3;
+    body_force(s, 0.0); /* no motion until orc_set_excitation: g_eff = g */
     s->nf = nf;
     s->nw = nw;
     s->cs = 2.0 * P->h;
@@ -846,3 +863,12 @@ int32_t orc_threads(void)
     return 1;
 #endif
 }
+
+void orc_set_excitation(orc_sim* s, const double amp[3], double freq)
+{
+    for (int d = 0; d < 3; d++) s->ex_amp[d] = amp[d];
+    s->ex_freq = freq;
+    body_force(s, s->t);
+}
+
+double orc_time(const orc_sim* s) { return s->t; }

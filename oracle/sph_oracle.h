@@ -75,6 +75,10 @@ void orc_destroy(orc_sim* s);
 /* advance nsteps; dt > 0 fixes the step, otherwise CFL; returns last dt */
 double orc_step(orc_sim* s, int32_t nsteps, double dt);
 void orc_reinit_density(orc_sim* s);
+/* rigid sinusoidal tank motion x = amp sin(2 pi freq t) from now on (t counts
+ * from creation), simulated in the tank frame (Sec. 4.2 excitation) */
+void orc_set_excitation(orc_sim* s, const double amp[3], double freq);
+double orc_time(const orc_sim* s);
 /* rates at the current state without advancing */
 void orc_rates(orc_sim* s, double* drho_dt, double* a);
 

@@ -487,3 +487,49 @@ def test_still_water_tank_stays_hydrostatic():
     sub = (w["pw"] != 0) & (zw < H - 3 * sc.dp)
     assert np.max(np.abs(w["pw"][sub] - 1000.0 * G * (H - zw[sub]))) < 0.02 * 1000.0 * G * H
     assert o.diagnostics()[0] == d0[0]
+
+
+# ------------------------------------------------------ tank excitation
+def test_excitation_free_particle_closed_form():
+    """A lone particle in a tank moving as x = amp sin(w t) (simulated in the
+    tank frame, body force g + amp w^2 sin(w t)): x(t) = x0 + v0 t + g t^2/2 +
+    amp (w t - sin w t), v(t) = v0 + g t + amp w (1 - cos w t); KDK is second
+    order, so 3000 steps of 1e-4 s stay within 1e-8 m (the particle stays
+    inside the grid, 40 cells of 2h around its start)."""
+    sc = S.jittered_blob(n=(1, 1, 1), jitter=0.0, vel_scale=0.0, margin_cells=40)
+    sc.g = (0.0, 0.0, -9.81)
+    sc.fluid_vel = np.array([[0.05, 0.0, 0.1]])
+    amp, f = np.array([0.1, 0.0, 0.02]), 0.496
+    o = oracle.OracleSim(sc, rho=np.array([1000.0]))
+    o.set_excitation(amp, f)
+    n, dt = 3000, 1e-4
+    o.step(n, dt)
+    t = o.time
+    assert t == pytest.approx(n * dt, rel=1e-12)
+    w = 2 * np.pi * f
+    g = np.array(sc.g)
+    x = sc.fluid_pos[0] + sc.fluid_vel[0] * t + 0.5 * g * t * t + amp * (w * t - np.sin(w * t))
+    v = sc.fluid_vel[0] + g * t + amp * w * (1 - np.cos(w * t))
+    st = o.fluid()
+    assert np.abs(st["x"][0] - x).max() < 1e-8
+    assert np.abs(st["v"][0] - v).max() < 1e-7
+
+
+def test_wall_pressure_extrapolation_with_a_tilted_body_force():
+    """With g = (3, 0, -9.81) (a tank accelerating along -x, seen in its frame)
+    and the matching linear field p_f = rho0 g.(r_f - r_ref), the extrapolation
+    (g.r_wf weighted by rho_f) reproduces p(r_w) = rho0 g.(r_w - r_ref) at every
+    supported wall particle, whatever the weights."""
+    sc = S.still_water_tank(n_fluid=(8, 8, 8), eos="linear")
+    sc.c0 = 1e4
+    g = np.array([3.0, 0.0, -9.81])
+    sc.g = tuple(g)
+    r_ref = np.array([0.0, 0.0, sc.phases[0].z_top])
+    p_f = 1000.0 * (sc.fluid_pos - r_ref) @ g
+    rho = 1000.0 + p_f / sc.c0 ** 2
+    o = oracle.OracleSim(sc, rho=rho)
+    pw = o.wall()["pw"]
+    has = pw != 0.0
+    assert has.sum() > 300
+    expect = 1000.0 * (sc.wall_pos[has] - r_ref) @ g
+    assert np.max(np.abs(pw[has] - expect)) < 1e-6 * 1000 * 9.81 * 0.1
