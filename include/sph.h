@@ -211,6 +211,21 @@ sph_status sph_diagnostics(sph_ctx* ctx, double out[8]);
  * SPH_ERR_CUDA, SPH_ERR_STATE. */
 sph_status sph_diagnostics_async(sph_ctx* ctx, double* out, int32_t where);
 
+/* Rigid sinusoidal motion of the tank (all wall particles), x_w(t) = x_w(0) +
+ * amp sin(2 pi freq t), t counted from sph_create -- the excitation of the
+ * sloshing case of Sec. 4.2.  The run proceeds in the tank's frame, where the
+ * walls stay fixed and the body force becomes g - d2x/dt2 = g + amp (2 pi
+ * freq)^2 sin(2 pi freq t), evaluated at t^{n+1} in the momentum equation and
+ * in the (g - a_w) term of Eq. (wallPressure); fluid velocities relative to
+ * the walls enter the Riemann states unchanged.  Positions and velocities are
+ * reported in the tank frame (add amp sin(2 pi freq t), amp 2 pi freq
+ * cos(2 pi freq t) for the laboratory frame).  amp = 0 or freq = 0 stops the
+ * motion.  Synchronises.  Errors: SPH_ERR_ARG, SPH_ERR_CUDA, SPH_ERR_STATE. */
+sph_status sph_set_excitation(sph_ctx* ctx, const double amp[3], double freq);
+
+/* Simulated time since sph_create (the sum of the steps' dt).  Synchronises. */
+sph_status sph_time(sph_ctx* ctx, double* t);
+
 /* Counters since creation: steps taken and the summed number of wall
  * particles that had fluid support in each step's wall-pressure sweep.
  * Either pointer may be NULL.  Synchronises. */

@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
     const T* __restrict__ drho, const int4* __restrict__ cell, const V4<T>* __restrict__ wpos,
     const V2<T>* __restrict__ wrho, const V4<T>* __restrict__ wnrm, const T* __restrict__ wc,
     const V4<T>* __restrict__ tA, const V4<T>* __restrict__ gx_in, const V4<T>* __restrict__ gv_in,
-    V4<T>* __restrict__ tX, V4<T>* __restrict__ tV, double* gparam)
+    const V4<T>* __restrict__ geff, V4<T>* __restrict__ tX, V4<T>* __restrict__ tV, double* gparam)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / LP;
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
     double gc0 = 0.0, ggp = 0.0, gmu = 0.0;
     if (i < n) {
         const PhaseK<T>& P = C.ph[0];
-        const V4<T> pi = pos[i], vi = vel[i], Ai = tA[i];
+        const V4<T> pi = pos[i], vi = vel[i], Ai = tA[i], ge = *geff;
         const int4 c = cell[i];
         const T rho_i = vi.w, p_i = pi.w, m = P.m;
         const T inv_rho_i = T(1) / rho_i;
@@ -402,14 +402,14 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
                     const T R = r2 * rinv;
                     T W, F;
                     kernel_WF(C, R, W, F);
-                    const T gr = C.gx * rx + C.gy * ry + C.gz * rz;
+                    const T gr = ge.x * rx + ge.y * ry + ge.z * rz;
                     pb += cw * W;
                     rb -= cw * gr * W;
                     const T k = cw * (p_i - rho_i * gr - pw.w) * F;
                     const T kg = -cw * rho_i * W;
-                    xx += kg * C.gx + k * rx;
-                    xy += kg * C.gy + k * ry;
-                    xz += kg * C.gz + k * rz;
+                    xx += kg * ge.x + k * rx;
+                    xy += kg * ge.y + k * ry;
+                    xz += kg * ge.z + k * rz;
                 }
             });
         pb += sp * inv_rho_i;

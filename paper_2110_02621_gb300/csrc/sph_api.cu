@@ -204,6 +204,25 @@ sph_status sph_diagnostics_async(sph_ctx* ctx, double* out, int32_t where)
     return ctx->sim->diagnostics_async(out, where);
 }
 
+sph_status sph_set_excitation(sph_ctx* ctx, const double amp[3], double freq)
+{
+    sph_status s = usable(ctx);
+    if (s != SPH_OK) return s;
+    if (!amp || !finite3(amp) || !(freq >= 0.0) || !std::isfinite(freq)) {
+        ctx->sim->err = "amp must be finite and freq finite and >= 0";
+        return SPH_ERR_ARG;
+    }
+    return ctx->sim->set_excitation(amp, freq);
+}
+
+sph_status sph_time(sph_ctx* ctx, double* t)
+{
+    sph_status s = usable(ctx);
+    if (s != SPH_OK) return s;
+    if (!t) return SPH_ERR_ARG;
+    return ctx->sim->time(t);
+}
+
 sph_status sph_counters(sph_ctx* ctx, int64_t* steps, int64_t* active_wall_steps)
 {
     sph_status s = usable(ctx);

@@ -44,7 +44,9 @@ struct Cfg {
     T inv_sigma0;           // 1 / (lattice number density)
     T sigma0_hi, sigma0_lo; // lattice number density sigma^0 as an unevaluated sum
     T inv_vol_hi, inv_vol_lo;  // 1/vol likewise (summation-density reference)
-    T cfl, body_dt;         // cfl, cfl*sqrt(h/|g|) (0 if g = 0)
+    T cfl, body_dt;         // cfl, cfl*sqrt(h/(|g| + |amp| w^2)) (0 if both vanish)
+    double g64[3];          // g in FP64 (for the body force of a moving tank)
+    double ex_amp[3], ex_w; // rigid tank motion x = amp sin(w t), w = 2 pi f (Sec. 4.2)
     int32_t nx, ny, nz, n_cells;
     int32_t n_phases;
     PhaseK<T> ph[2];

@@ -45,6 +45,8 @@ struct SimBase {
     virtual sph_status profile(uint32_t mask) = 0;
     virtual sph_status profile_read(double* ms, int64_t* timed, int64_t* launches) = 0;
     virtual sph_status tape(int32_t nsteps, double dt, double* dt_out) = 0;
+    virtual sph_status set_excitation(const double amp[3], double freq) = 0;
+    virtual sph_status time(double* t) = 0;
     virtual sph_status backward(const sph_adjoint_seed& seed, sph_adjoint_grad& grad, int32_t where) = 0;
 
     std::string err;

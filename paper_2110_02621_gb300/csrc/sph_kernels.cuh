@@ -55,15 +55,31 @@ __device__ __forceinline__ T step_dt(const Cfg<T>& C, const T* dt_fixed, const u
 // counters of the coming re-binning.
 template <class T>
 __global__ void k_begin_step(Cfg<T> C, const T* __restrict__ dt_fixed, unsigned long long* vmax_bits,
-                             T* d_dt, int32_t* counts, int32_t n_counts, int32_t* d_tag)
+                             T* d_dt, int32_t* counts, int32_t n_counts, int32_t* d_tag, double* d_time,
+                             V4<T>* d_geff)
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t == 0) {
         *d_tag += 1;  // new wall-support tag for this step's neighbour build
-        *d_dt = step_dt(C, dt_fixed, vmax_bits);
+        const T dt = step_dt(C, dt_fixed, vmax_bits);
+        *d_dt = dt;
         *vmax_bits = 0ull;
+        advance_time(C, dt, d_time, d_geff);
     }
     for (int k = t; k < n_counts; k += gridDim.x * blockDim.x) counts[k] = 0;
+}
+
+// Advance the simulated time by the step's dt and set the body force of
+// t^{n+1} for the sweeps: in the frame of a tank moving as x = amp sin(w t)
+// it is g - d2x/dt2 = g + amp w^2 sin(w t) (Sec. 4.2); g without motion.
+template <class T>
+__device__ __forceinline__ void advance_time(const Cfg<T>& C, T dt, double* d_time, V4<T>* d_geff)
+{
+    const double t = *d_time + (double)dt;
+    *d_time = t;
+    const double k = C.ex_w * C.ex_w * sin(C.ex_w * t);
+    *d_geff = V4<T>{(T)(C.g64[0] + C.ex_amp[0] * k), (T)(C.g64[1] + C.ex_amp[1] * k),
+                    (T)(C.g64[2] + C.ex_amp[2] * k), T(0)};
 }
 
 // half kick and drift of one particle, then move the offset back into its
@@ -87,15 +103,16 @@ __device__ __forceinline__ void kick_drift(const Cfg<T>& C, T dt, V4<T>& p, V4<T
 // v^{n+1/2} = v^n + dt/2 a^n, r^{n+1} = r^n + dt v^{n+1/2} (Sec. 2.6), new cell
 // and its occupancy count; bucket n_cells collects particles outside the grid.
 // Every thread evaluates the step's dt; thread 0 publishes it for the later
-// kernels and opens the step's wall-support tag.  (U_max is cleared by the
+// kernels, opens the step's wall-support tag and advances the time and the
+// body force.  (U_max is cleared by the
 // scatter that follows, once every thread here has read it.)
 template <class T, bool KAHAN>
 __global__ void k_predict(Cfg<T> C, int32_t n, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel,
                           const V4<T>* __restrict__ acc, const V4<T>* __restrict__ comp,
                           const int4* __restrict__ cell, const T* __restrict__ dt_fixed,
                           const unsigned long long* __restrict__ vmax_bits, T* __restrict__ d_dt,
-                          int32_t* __restrict__ d_tag, int4* __restrict__ newcell, int32_t* __restrict__ rank,
-                          int32_t* counts)
+                          int32_t* __restrict__ d_tag, double* __restrict__ d_time, V4<T>* __restrict__ d_geff,
+                          int4* __restrict__ newcell, int32_t* __restrict__ rank, int32_t* counts)
 {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -103,6 +120,7 @@ __global__ void k_predict(Cfg<T> C, int32_t n, const V4<T>* __restrict__ pos, co
     if (s == 0) {
         *d_dt = dt;
         *d_tag += 1;
+        advance_time(C, dt, d_time, d_geff);
     }
     V4<T> p = pos[s], v = vel[s], a = acc[s], cm = comp[s];
     int4 c = cell[s];

@@ -70,6 +70,17 @@ inline double lattice_sigma0(double dp, double h, int dim)
     return s;
 }
 
+// body-force limit of the time step (Sec. 2.6), with the largest body force
+// of the tank motion, |g| + |amp| w^2
+template <class T>
+void set_body_dt(Cfg<T>& C, double cfl, double h)
+{
+    double gn = std::sqrt(C.g64[0] * C.g64[0] + C.g64[1] * C.g64[1] + C.g64[2] * C.g64[2]);
+    gn += std::sqrt(C.ex_amp[0] * C.ex_amp[0] + C.ex_amp[1] * C.ex_amp[1] + C.ex_amp[2] * C.ex_amp[2]) * C.ex_w *
+          C.ex_w;
+    C.body_dt = gn > 0.0 ? (T)(cfl * std::sqrt(h / gn)) : T(0);
+}
+
 template <class T>
 Cfg<T> make_cfg(const sph_params& P, const int32_t dims[3])
 {
@@ -106,8 +117,12 @@ Cfg<T> make_cfg(const sph_params& P, const int32_t dims[3])
     C.inv_vol_hi = (T)inv_vol;
     C.inv_vol_lo = (T)(inv_vol - (double)C.inv_vol_hi);
     C.cfl = (T)P.cfl;
-    double gn = std::sqrt(P.g[0] * P.g[0] + P.g[1] * P.g[1] + P.g[2] * P.g[2]);
-    C.body_dt = gn > 0.0 ? (T)(P.cfl * std::sqrt(h / gn)) : T(0);
+    for (int d = 0; d < 3; ++d) {
+        C.g64[d] = P.g[d];
+        C.ex_amp[d] = 0.0;
+    }
+    C.ex_w = 0.0;
+    set_body_dt(C, P.cfl, h);
     C.nx = dims[0];
     C.ny = dims[1];
     C.nz = dims[2];
@@ -235,6 +250,14 @@ class Sim final : public SimBase {
         SPH_CUDA(cudaMemsetAsync(d_dt_, 0, sizeof(T), stream));
         SPH_CUDA(cudaMemsetAsync(d_dt_fixed_, 0, sizeof(T), stream));
         SPH_CUDA(cudaMemsetAsync(d_vmax_, 0, sizeof(unsigned long long), stream));
+        {
+            // t = 0, body force g
+            const V4<T> g0{C_.gx, C_.gy, C_.gz, T(0)};
+            const double t0 = 0.0;
+            SPH_CUDA(cudaMemcpyAsync(d_geff_, &g0, sizeof g0, cudaMemcpyHostToDevice, stream));
+            SPH_CUDA(cudaMemcpyAsync(d_time_, &t0, sizeof t0, cudaMemcpyHostToDevice, stream));
+            SPH_CUDA(cudaStreamSynchronize(stream));
+        }
         SPH_CUDA(cudaMemsetAsync(d_flags_, 0, sizeof(int32_t), stream));
         SPH_CUDA(cudaMemsetAsync(d_active_, 0, sizeof(unsigned long long), stream));
         SPH_CUDA(cudaMemsetAsync(d_tag_, 0, sizeof(int32_t), stream));
@@ -365,6 +388,36 @@ class Sim final : public SimBase {
         return SPH_OK;
     }
 
+    // Rigid sinusoidal tank motion from now on (Sec. 4.2 excitation): the
+    // body force of later steps follows amp w^2 sin(w t); the captured step
+    // graphs hold the old constants and are dropped.
+    sph_status set_excitation(const double amp[3], double freq) override
+    {
+        if (P_.dim == 2 && amp[1] != 0.0) {
+            err = "dim = 2: the motion must lie in the x-z plane";
+            return SPH_ERR_ARG;
+        }
+        for (int d = 0; d < 3; ++d) C_.ex_amp[d] = D_.ex_amp[d] = amp[d];
+        C_.ex_w = D_.ex_w = 2.0 * 3.14159265358979323846 * freq;
+        set_body_dt(C_, P_.cfl, P_.h);
+        set_body_dt(D_, P_.cfl, P_.h);
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        for (cudaGraphExec_t& g : gexec_)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
+        return SPH_OK;
+    }
+
+    sph_status time(double* t) override
+    {
+        SPH_CUDA(cudaMemcpyAsync(&host_status_->time, d_time_, sizeof(double), cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        *t = host_status_->time;
+        return SPH_OK;
+    }
+
     // ------------------------------------------------------------ adjoint
     sph_status tape(int32_t nsteps, double dt, double* dt_out) override
     {
@@ -481,7 +534,8 @@ class Sim final : public SimBase {
                 SPH_KERNEL(SPH_K_ADJ_MOMENTUM, 1,
                            k_adj_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                                C_, nf_, dt, 0, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_[p], drho_[0],
-                               cell_[q], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], tX_, tV_, adj_param_));
+                               cell_[q], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], d_geff_, tX_, tV_,
+                               adj_param_));
                 SPH_KERNEL(SPH_K_ADJ_CONTINUITY, 1,
                            k_adj_continuity<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                                C_, nf_, dt, c.reinit ? 1 : 0, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[1], vel_[p],
@@ -513,7 +567,8 @@ class Sim final : public SimBase {
             SPH_KERNEL(SPH_K_ADJ_MOMENTUM, 1,
                        k_adj_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                            C_, nf_, T(0), 1, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_[p0], drho_[0],
-                           cell_[p0], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], tX_, tV_, adj_param_));
+                           cell_[p0], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], d_geff_, tX_, tV_,
+                           adj_param_));
             SPH_KERNEL(SPH_K_ADJ_OTHER, 1,
                        k_adj_export<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, id_[p0], tX_, tV_, ox, ov, orho));
         }
@@ -684,6 +739,7 @@ class Sim final : public SimBase {
         T dt, dt_fixed;
         unsigned long long active;
         double diag[8];
+        double time;
     };
     struct EvPair {
         cudaEvent_t a, b;
@@ -752,6 +808,8 @@ class Sim final : public SimBase {
         if ((s = alloc(d_dt_, 1)) != SPH_OK) return s;
         if ((s = alloc(d_dt_fixed_, 1)) != SPH_OK) return s;
         if ((s = alloc(d_vmax_, 1)) != SPH_OK) return s;
+        if ((s = alloc(d_time_, 1)) != SPH_OK) return s;
+        if ((s = alloc(d_geff_, 1)) != SPH_OK) return s;
         if ((s = alloc(d_flags_, 1)) != SPH_OK) return s;
         if ((s = alloc(d_active_, 1)) != SPH_OK) return s;
         if ((s = alloc(diag_partial_, 8 * (size_t)grid_for(nf_ > 0 ? nf_ : 1))) != SPH_OK) return s;
@@ -777,7 +835,7 @@ class Sim final : public SimBase {
                    k_wall_pressure<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(C_, nw_, fstart_, wpos_,
                                                                                          wcell_, pos_[0],
                                                                            vel_cur, wrho_, wtag_, d_tag_,
-                                                                           d_active_));
+                                                                           d_geff_, d_active_));
         return SPH_OK;
     }
 
@@ -789,7 +847,7 @@ class Sim final : public SimBase {
         SPH_KERNEL(SPH_K_MOMENTUM, 1,
                    k_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                        C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_cur, cell, phase, wpos_, wrho_, wnrm_,
-                       d_dt_, acc_, vel_out, sigma_, d_vmax_, d_flags_));
+                       d_dt_, d_geff_, acc_, vel_out, sigma_, d_vmax_, d_flags_));
         return SPH_OK;
     }
 
@@ -809,11 +867,11 @@ class Sim final : public SimBase {
             SPH_KERNEL(SPH_K_PREDICT, 1,
                        k_predict<T, KAHAN><<<grid_for(nf_), BLOCK, 0, stream>>>(
                            C_, nf_, pos_[0], vel_[p], acc_, comp_[p], cell_[p], d_dt_fixed_, d_vmax_, d_dt_, d_tag_,
-                           newcell_, rank_, counts_));
+                           d_time_, d_geff_, newcell_, rank_, counts_));
         else
             SPH_KERNEL(SPH_K_BEGIN_STEP, 1,
                        k_begin_step<T><<<grid_for(n_cells_ + 1), BLOCK, 0, stream>>>(
-                           C_, d_dt_fixed_, d_vmax_, d_dt_, counts_, n_cells_ + 1, d_tag_));
+                           C_, d_dt_fixed_, d_vmax_, d_dt_, counts_, n_cells_ + 1, d_tag_, d_time_, d_geff_));
         int nscan = 0;
         SPH_KERNEL(SPH_K_SCAN, nscan, nscan = scan_exclusive(counts_, n_cells_ + 1, fstart_, sums_, stream, counts_));
         if (nf_ > 0) {
@@ -891,6 +949,8 @@ class Sim final : public SimBase {
         int32_t *id = nullptr, *phase = nullptr, *fstart = nullptr;
         V2<T>* wrho = nullptr;
         unsigned long long *vmax = nullptr, *active = nullptr;
+        double* time = nullptr;
+        V4<T>* geff = nullptr;
         int par = 0;
         int64_t steps = 0;
         T dt = T(0);
@@ -914,7 +974,8 @@ class Sim final : public SimBase {
                          o_ph = take(nf * sizeof(int32_t)), o_wpos = take(nw * sizeof(V4<T>)),
                          o_wrho = take(nw * sizeof(V2<T>)), o_vm = take(sizeof(unsigned long long)),
                          o_ac = take(sizeof(unsigned long long)),
-                         o_fs = take(((size_t)n_cells_ + 2) * sizeof(int32_t)), o_dt = take(sizeof(T));
+                         o_fs = take(((size_t)n_cells_ + 2) * sizeof(int32_t)), o_dt = take(sizeof(T)),
+                         o_tm = take(sizeof(double)), o_ge = take(sizeof(V4<T>));
             sph_status s = alloc(c.buf, off);
             if (s != SPH_OK) return s;
             c.pos = (V4<T>*)(c.buf + o_pos);
@@ -932,6 +993,8 @@ class Sim final : public SimBase {
             c.active = (unsigned long long*)(c.buf + o_ac);
             c.fstart = (int32_t*)(c.buf + o_fs);
             c.dtd = (T*)(c.buf + o_dt);
+            c.time = (double*)(c.buf + o_tm);
+            c.geff = (V4<T>*)(c.buf + o_ge);
         }
         c.par = par_;
         c.steps = steps_;
@@ -967,6 +1030,8 @@ class Sim final : public SimBase {
         add(d_vmax_, c.vmax, sizeof(unsigned long long));
         add(d_active_, c.active, sizeof(unsigned long long));
         add(fstart_, c.fstart, ((size_t)n_cells_ + 2) * sizeof(int32_t));
+        add(d_time_, c.time, sizeof(double));
+        add(d_geff_, c.geff, sizeof(V4<T>));
         const int64_t want = (int64_t)((L.total / 4 + 255) / 256);
         const int nb = (int)(want < 1 ? 1 : (want > 152 * 8 ? 152 * 8 : want));
         SPH_KERNEL(SPH_K_ADJ_OTHER, 1, k_copy_segments<<<nb, 256, 0, stream>>>(L));
@@ -1065,6 +1130,8 @@ class Sim final : public SimBase {
     T* d_dt_ = nullptr;
     T* d_dt_fixed_ = nullptr;
     unsigned long long* d_vmax_ = nullptr;
+    double* d_time_ = nullptr;  // simulated time since create
+    V4<T>* d_geff_ = nullptr;   // body force of the current step (g, or g + amp w^2 sin(w t))
     int32_t* d_flags_ = nullptr;
     unsigned long long* d_active_ = nullptr;
     double* diag_partial_ = nullptr;

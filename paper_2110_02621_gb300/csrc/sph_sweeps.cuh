@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
     Cfg<T> C, int32_t nw, const int32_t* __restrict__ fstart, V4<T>* __restrict__ wpos,
     const int4* __restrict__ wcell, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel,
     V2<T>* __restrict__ wrho, const int32_t* __restrict__ wtag, const int32_t* __restrict__ d_tag,
-    unsigned long long* active)
+    const V4<T>* __restrict__ geff, unsigned long long* active)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int w = t / LP;
@@ -405,6 +405,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
         const bool multi = C.n_phases > 1;
         T num = T(0), den = T(0);
         if (wtag[w] == *d_tag) {
+            const V4<T> ge = *geff;
             const int4 c = wcell[w];
             const V4<T> pw = wpos[w];
             scan_compact(C, c, pw, fstart, pos, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
@@ -412,7 +413,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
                 const T p_f = reinterpret_cast<const T*>(pos + j)[3];
                 const T rho_f = vel[j].w;
                 const T om = multi ? p_div(W, rho_f) : W;
-                num += (p_f + rho_f * (C.gx * rx + C.gy * ry + C.gz * rz)) * om;
+                num += (p_f + rho_f * (ge.x * rx + ge.y * ry + ge.z * rz)) * om;
                 den += om;
             });
             num = group_sum(num);
@@ -436,7 +437,8 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
 // or Eq. (RSatWall) (wall); per pair -2 m_j p*/(rho_i rho_j) F r_ij, where
 //   p*/(rho_i rho_j) = (p_i/rho_i + p_j/rho_j + beta dU)/(rho_i + rho_j),
 //   dU = U_L - U_R = -v_ij.r_ij/r, beta = min(3 max(dU, 0), c).
-// Plus gravity, the Morris viscous term, and the penalty force of
+// Plus the body force (g, or g + amp w^2 sin(w t) in a moving tank's frame),
+// the Morris viscous term, and the penalty force of
 // Eq. (SPH_penaltyMethodTerm) with delta = 2|r_iw.n_w|/dx, lambda from
 // Eq. (symbc) and dx^3 restoring its units.  Then the final kick
 // v^{n+1} = v^{n+1/2} + dt/2 a^{n+1}, the number density sigma(r^{n+1}) for
@@ -449,8 +451,9 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
     const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw, const int32_t* __restrict__ cnt,
     const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel, const int4* __restrict__ cell,
     const int32_t* __restrict__ phase, const V4<T>* __restrict__ wpos, const V2<T>* __restrict__ wrho,
-    const V4<T>* __restrict__ wnrm, const T* __restrict__ d_dt, V4<T>* __restrict__ acc,
-    V4<T>* __restrict__ vel_o, T* __restrict__ dsig_o, unsigned long long* vmax_bits, int32_t* flags)
+    const V4<T>* __restrict__ wnrm, const T* __restrict__ d_dt, const V4<T>* __restrict__ geff,
+    V4<T>* __restrict__ acc, V4<T>* __restrict__ vel_o, T* __restrict__ dsig_o, unsigned long long* vmax_bits,
+    int32_t* flags)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / LP;
@@ -529,9 +532,10 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
                     }
                     kahan_add(sg, se, W);
                 });
-            ax = group_sum(ax) + C.gx;
-            ay = group_sum(ay) + C.gy;
-            az = group_sum(az) + C.gz;
+            const V4<T> ge = *geff;
+            ax = group_sum(ax) + ge.x;
+            ay = group_sum(ay) + ge.y;
+            az = group_sum(az) + ge.z;
             group_kahan(sg, se);
             const V4<T> vo{fma_rn(hdt, ax, vi.x), fma_rn(hdt, ay, vi.y), fma_rn(hdt, az, vi.z), rho_i};
             bad = !(f_finite(ax) && f_finite(ay) && f_finite(az));

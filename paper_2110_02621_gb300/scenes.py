@@ -371,6 +371,31 @@ def two_phase_hydrostatic_tank_2d(dx: float = 0.01, L: float = 1.0, H: float = 0
         wall_pos=wall, reinit_every=1, steps=1, dim=2)
 
 
+def sloshing_tank_2d(dx: float = 0.01, L: float = 1.3, D: float = 0.9, H: float = 0.18,
+                     layers: int = 3, air_penalty: bool = True) -> Scene:
+    """The two-phase sloshing tank of Sec. 4.2 in the x-z plane: a closed tank
+    of width L = 1.3 m and height D = 0.9 m, water (rho0 = 1000) to H = 0.18 m,
+    air (rho0 = 1) above, at rest; the paper drives it with x = A0 sin(2 pi f0
+    t), A0 = 0.1 m, f0 = 0.496 Hz (sph_set_excitation).  Linear EOS with one
+    c0 = 10 sqrt(g H); air with summation density and, unless turned off, the
+    penalty force of Eq. (SPH_penaltyMethodTerm)."""
+    nx, nz = _count(L, dx), _count(D, dx)
+    h = 1.3 * dx
+    fluid = lattice2d((nx, nz), dx)
+    phase = np.where(fluid[:, 2] < H, 0, 1).astype(np.int32)
+    wall = box_walls2d((nx, nz), dx, layers, roof=True)
+    lo, hi = _domain2d(wall, fluid, 2 * h, 0.0)
+    return Scene(
+        name=f"sloshing_tank_2d_dx{dx:g}", dp=dx, h=h, c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G),
+        lo=lo, hi=hi,
+        phases=[Phase(rho0=1000.0, eos="linear", density="continuity", reinit="free_surface",
+                      penalty=False, z_top=H),
+                Phase(rho0=1.0, eos="linear", density="summation", reinit="internal",
+                      penalty=air_penalty, z_top=D)],
+        fluid_pos=fluid, fluid_vel=np.zeros_like(fluid), fluid_phase=phase, wall_pos=wall,
+        reinit_every=1, steps=1, dim=2)
+
+
 def dam_break_2d(tank: Tuple[float, float] = (0.4, 0.3), column: Tuple[float, float] = (0.15, 0.15),
                  dx: float = 0.005, layers: int = 3, penalty: bool = True, reinit_every: int = 20) -> Scene:
     """A 2-D dam break in the x-z plane: a water column at x = 0 in an open

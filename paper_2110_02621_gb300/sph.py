@@ -28,7 +28,7 @@ EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_grid_info", "sph_get_cells", "sph_diagnostics", "sph_counters",
            "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_bin_sort_noalloc",
            "sph_profile", "sph_profile_read", "sph_tape", "sph_backward", "sph_step_async",
-           "sph_sync", "sph_diagnostics_async")
+           "sph_sync", "sph_diagnostics_async", "sph_set_excitation", "sph_time")
 SPH_ERR_CAPACITY = 8
 SPH_BIN_SORT_NOALLOC_SCRATCH = 32 << 20
 KERNEL_KINDS = ("begin_step", "predict", "scan", "scatter", "gather", "neighbors",
@@ -117,6 +117,8 @@ def lib() -> C.CDLL:
         L.sph_step_async.argtypes = [p, i32, d]
         L.sph_sync.argtypes = [p, p]
         L.sph_diagnostics_async.argtypes = [p, p, i32]
+        L.sph_set_excitation.argtypes = [p, p, d]
+        L.sph_time.argtypes = [p, p]
         L.sph_backward.argtypes = [p, p, p, i32]
         for name in EXPORTS:
             if name not in ("sph_last_error", "sph_destroy"):
@@ -329,6 +331,17 @@ class Simulation:
 
     def reinit_density(self):
         _check(sph_reinit_density(self.ctx), self.ctx)
+
+    def set_excitation(self, amp, freq: float):
+        """Rigid tank motion x = amp sin(2 pi freq t) (sph_set_excitation)."""
+        a = np.ascontiguousarray(amp, np.float64)
+        _check(lib().sph_set_excitation(self.ctx, _ptr(a), float(freq)), self.ctx)
+
+    @property
+    def time(self) -> float:
+        t = C.c_double(0.0)
+        _check(lib().sph_time(self.ctx, C.byref(t)), self.ctx)
+        return t.value
 
     def state(self) -> dict:
         n, m = self.nf, self.nw

@@ -455,3 +455,39 @@ def test_2d_input_checks():
     with pytest.raises(sph.SphError) as e:
         sph.Simulation(sc)
     assert e.value.status == sph.SPH_ERR_ARG
+
+
+# ------------------------------------------------------ tank excitation
+def test_excitation_parity_and_free_particle():
+    """Rigid tank motion (sph_set_excitation, Sec. 4.2) against the oracle: a
+    small two-phase 2-D tank driven at 0.5 Hz with amplitude 0.1 m (first
+    step within the single-step tolerance, then 100 steps), and a lone
+    particle against the closed form of its motion in the tank frame."""
+    sc = S.two_phase_hydrostatic_tank_2d(dx=0.02, L=0.6, H=0.2)
+    light = np.array([sc.phases[p].density == "summation" for p in range(len(sc.phases))])[sc.fluid_phase]
+    ref = oracle.OracleSim(sc)
+    ref.set_excitation([0.1, 0.0, 0.05], 0.5)
+    with sph.Simulation(sc) as sim:
+        sim.set_excitation([0.1, 0.0, 0.05], 0.5)
+        dt = sim.step(1)
+        assert abs(dt - ref.step(1)) <= 1e-6 * dt
+        o = ref.fluid()
+        check_state(sim.state(), o, ref.wall(), sc.dp, tol_rate=5e-5, what="first step", light=light,
+                    floor=light_floor(sc), heavy_abs=heavy_floor(sc, o))
+        sim.step(100)
+        ref.step(100)
+        assert sim.time == pytest.approx(ref.time, rel=1e-6)
+        g, o = sim.state(), ref.fluid()
+        assert np.abs(g["x"] - o["x"]).max() <= TOL_X * sc.dp
+        assert rel_inf(g["rho"], o["rho"]) <= 1e-5
+    lone = S.jittered_blob(n=(1, 1, 1), jitter=0.0, vel_scale=0.0, margin_cells=40)
+    lone.g = (0.0, 0.0, -9.81)
+    lone.fluid_vel = np.array([[0.05, 0.0, 0.1]])
+    amp, f = np.array([0.1, 0.0, 0.02]), 0.496
+    with sph.Simulation(lone, precision=sph.SPH_FP64_PLAIN, rho=np.array([1000.0])) as sim:
+        sim.set_excitation(amp, f)
+        sim.step(3000, 1e-4)
+        t, st = sim.time, sim.state()
+    w = 2 * np.pi * f
+    x = lone.fluid_pos[0] + lone.fluid_vel[0] * t + 0.5 * np.array(lone.g) * t * t + amp * (w * t - np.sin(w * t))
+    assert np.abs(st["x"][0] - x).max() < 1e-8
