@@ -80,6 +80,8 @@ def lib():
             "orc_diagnostics": (None, [p, p]), "orc_sigma0": (d, [p]),
             "orc_step_count": (i64, [p]), "orc_threads": (i32, []),
             "orc_set_excitation": (None, [p, p, d]), "orc_time": (d, [p]),
+            "orc_probe_pressure": (None, [p, p, i64, p, p]),
+            "orc_gauge_height": (None, [p, p, i64, d, p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -241,6 +243,22 @@ class OracleSim:
         out = np.zeros(8)
         lib().orc_diagnostics(self._h, _ptr(out))
         return out
+
+    def probe_pressure(self, pts):
+        """(p_bar, w) at the points pts (n x 3): Shepard-interpolated pressure
+        and kernel sum over the fluid particles (Sec. 4.3 sensors)."""
+        q = np.ascontiguousarray(pts, np.float64).reshape(-1, 3)
+        p, w = np.zeros(len(q)), np.zeros(len(q))
+        lib().orc_probe_pressure(self._h, _ptr(q), len(q), _ptr(p), _ptr(w))
+        return p, w
+
+    def gauge_height(self, gauges, dz: float):
+        """Free-surface height on each vertical line (x, y, z_lo, z_hi) of
+        gauges (n x 4), sampled dz apart (Sec. 4.3 wave gauges)."""
+        g = np.ascontiguousarray(gauges, np.float64).reshape(-1, 4)
+        H = np.zeros(len(g))
+        lib().orc_gauge_height(self._h, _ptr(g), len(g), float(dz), _ptr(H))
+        return H
 
     @property
     def sigma0(self) -> float:
