@@ -226,6 +226,47 @@ sph_status sph_set_excitation(sph_ctx* ctx, const double amp[3], double freq);
 /* Simulated time since sph_create (the sum of the steps' dt).  Synchronises. */
 sph_status sph_time(sph_ctx* ctx, double* t);
 
+/* Pressure sensors (the sensors P_i of Sec. 4.3).  The paper defers the
+ * sampling to the work it cites; the operation here is the kernel-weighted,
+ * Shepard-normalised interpolation over fluid particles: for each point r_k
+ * (pts[3k..3k+2], absolute coordinates)
+ *   w_k = sum_j V_j W(|r_k - r_j|),  V_j = m_j / rho_j,
+ *   p_k = sum_j p_j V_j W(|r_k - r_j|) / w_k   (p_k = 0 where w_k = 0),
+ * j over every fluid particle of every phase inside the grid with
+ * |r_k - r_j| < 2h (r = r_j included), W the Wendland C2 kernel of the run's
+ * dimension; evaluated in FP64 from the current state, between steps.  w_k is
+ * the fluid's volume fraction at r_k (about 1 inside the fluid, 1/2 on a flat
+ * free surface or a wall face).  Points may lie anywhere, outside the grid
+ * included.  p and w (n doubles each; either may be NULL) receive the results.
+ * where = SPH_HOST: pts, p and w are host memory and the call synchronises;
+ * SPH_DEVICE: device memory, the work is enqueued on the stream and the call
+ * returns without waiting (results valid after sph_sync or any synchronising
+ * call), so that a sensor time series can be recorded between
+ * sph_step_async calls.  Errors: SPH_ERR_ARG (n < 0, pts NULL with n > 0, a
+ * non-finite host point), SPH_ERR_CUDA, SPH_ERR_STATE. */
+sph_status sph_probe_pressure(sph_ctx* ctx, const double* pts, int32_t n,
+                              double* p, double* w, int32_t where);
+
+enum { SPH_GAUGE_MAX_SAMPLES = 65536 };
+
+/* Wave-height gauges (the gauges H_i of Sec. 4.3).  For each vertical line
+ * gauges[4k..4k+3] = (x, y, z_lo, z_hi) (z along -g; in 2-D y is the plane's
+ * y), the liquid volume fraction phi(z) = sum_{j in phase 0} V_j
+ * W(|(x, y, z) - r_j|) is sampled at z_i = z_lo + i dz, i = 0..K,
+ * K = floor((z_hi - z_lo)/dz); the height is the highest sample with
+ * phi >= 1/2, moved to the linear interpolate of the crossing with the sample
+ * above: H = z_i + dz (phi_i - 1/2)/(phi_i - phi_{i+1}); H = z_lo when no
+ * sample reaches 1/2 (a dry line) and z_K when the top one does.  1/2 is the
+ * value of phi on the face of a half-space of particles, so H reads the free
+ * surface of the first phase (the liquid of a two-phase run); isolated drops
+ * (phi below 1/2) are not counted.  Evaluated in FP64 between steps.  H
+ * receives n doubles.  where as for sph_probe_pressure; with SPH_DEVICE a
+ * line that is not finite, has z_hi < z_lo or K >= SPH_GAUGE_MAX_SAMPLES
+ * yields NaN.  Errors: SPH_ERR_ARG (n < 0, NULL arrays with n > 0, dz not
+ * finite and > 0, such a line in host memory), SPH_ERR_CUDA, SPH_ERR_STATE. */
+sph_status sph_gauge_height(sph_ctx* ctx, const double* gauges, int32_t n,
+                            double dz, double* H, int32_t where);
+
 /* Counters since creation: steps taken and the summed number of wall
  * particles that had fluid support in each step's wall-pressure sweep.
  * Either pointer may be NULL.  Synchronises. */

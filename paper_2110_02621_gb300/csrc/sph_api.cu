@@ -223,6 +223,46 @@ sph_status sph_time(sph_ctx* ctx, double* t)
     return ctx->sim->time(t);
 }
 
+sph_status sph_probe_pressure(sph_ctx* ctx, const double* pts, int32_t n, double* p, double* w, int32_t where)
+{
+    sph_status s = usable(ctx);
+    if (s != SPH_OK) return s;
+    if (n < 0 || (n > 0 && !pts) || (where != SPH_HOST && where != SPH_DEVICE)) {
+        ctx->sim->err = "n must be >= 0, pts non-NULL when n > 0; where must be SPH_HOST or SPH_DEVICE";
+        return SPH_ERR_ARG;
+    }
+    if (where == SPH_HOST)
+        for (int32_t k = 0; k < n; ++k)
+            if (!finite3(pts + 3 * (size_t)k)) {
+                ctx->sim->err = "non-finite sensor position";
+                return SPH_ERR_ARG;
+            }
+    return ctx->sim->probe_pressure(pts, n, p, w, where);
+}
+
+sph_status sph_gauge_height(sph_ctx* ctx, const double* gauges, int32_t n, double dz, double* H, int32_t where)
+{
+    sph_status s = usable(ctx);
+    if (s != SPH_OK) return s;
+    if (n < 0 || (n > 0 && (!gauges || !H)) || !(dz > 0.0) || !std::isfinite(dz) ||
+        (where != SPH_HOST && where != SPH_DEVICE)) {
+        ctx->sim->err = "n must be >= 0, gauges and H non-NULL when n > 0, dz finite and > 0; where must be "
+                        "SPH_HOST or SPH_DEVICE";
+        return SPH_ERR_ARG;
+    }
+    if (where == SPH_HOST)
+        for (int32_t k = 0; k < n; ++k) {
+            const double* g = gauges + 4 * (size_t)k;
+            const bool fin = std::isfinite(g[0]) && std::isfinite(g[1]) && std::isfinite(g[2]) && std::isfinite(g[3]);
+            if (!fin || !(g[3] >= g[2]) || !(std::floor((g[3] - g[2]) / dz) < (double)SPH_GAUGE_MAX_SAMPLES)) {
+                ctx->sim->err = "gauge lines must be finite with z_lo <= z_hi and fewer than "
+                                "SPH_GAUGE_MAX_SAMPLES samples";
+                return SPH_ERR_ARG;
+            }
+        }
+    return ctx->sim->gauge_height(gauges, n, dz, H, where);
+}
+
 sph_status sph_counters(sph_ctx* ctx, int64_t* steps, int64_t* active_wall_steps)
 {
     sph_status s = usable(ctx);

@@ -47,6 +47,8 @@ struct SimBase {
     virtual sph_status tape(int32_t nsteps, double dt, double* dt_out) = 0;
     virtual sph_status set_excitation(const double amp[3], double freq) = 0;
     virtual sph_status time(double* t) = 0;
+    virtual sph_status probe_pressure(const double* pts, int32_t n, double* p, double* w, int32_t where) = 0;
+    virtual sph_status gauge_height(const double* g, int32_t n, double dz, double* H, int32_t where) = 0;
     virtual sph_status backward(const sph_adjoint_seed& seed, sph_adjoint_grad& grad, int32_t where) = 0;
 
     std::string err;

@@ -12,6 +12,7 @@
 
 #include "sph_internal.h"
 #include "sph_adjoint.cuh"
+#include "sph_probes.cuh"
 #include "sph_setup.cuh"
 
 namespace sph {
@@ -712,6 +713,60 @@ class Sim final : public SimBase {
         SPH_KERNEL(SPH_K_OTHER, 1, k_diag_final<<<1, 32, 0, stream>>>(nb, diag_partial_, diag_out_));
         SPH_CUDA(cudaMemcpyAsync(out, diag_out_, sizeof(double) * 8,
                                  where == SPH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, stream));
+        return SPH_OK;
+    }
+
+    // Sensors (Sec. 4.3) at n points; HOST: pts and outputs are host memory
+    // and the call synchronises; DEVICE: device memory, enqueued only.
+    sph_status probe_pressure(const double* pts, int32_t n, double* p, double* w, int32_t where) override
+    {
+        if (n == 0) return SPH_OK;
+        const bool host = where == SPH_HOST;
+        const size_t b1 = sizeof(double) * (size_t)n;
+        const double* dpts = pts;
+        double *dp = p, *dw = w, *scratch = nullptr;
+        if (host) {
+            SPH_CUDA(cudaMallocAsync(&scratch, 5 * b1, stream));
+            SPH_CUDA(cudaMemcpyAsync(scratch, pts, 3 * b1, cudaMemcpyHostToDevice, stream));
+            dpts = scratch;
+            dp = p ? scratch + 3 * (size_t)n : nullptr;
+            dw = w ? scratch + 4 * (size_t)n : nullptr;
+        }
+        const int64_t threads = (int64_t)n * 32;
+        SPH_KERNEL(SPH_K_OTHER, 1,
+                   k_probe_pressure<T><<<(unsigned)((threads + BLOCK - 1) / BLOCK), BLOCK, 0, stream>>>(
+                       D_, I_, n, dpts, fstart_, pos_[0], drho_[0], phase_[par_], dp, dw));
+        if (host) {
+            if (p) SPH_CUDA(cudaMemcpyAsync(p, dp, b1, cudaMemcpyDeviceToHost, stream));
+            if (w) SPH_CUDA(cudaMemcpyAsync(w, dw, b1, cudaMemcpyDeviceToHost, stream));
+            SPH_CUDA(cudaFreeAsync(scratch, stream));
+            SPH_CUDA(cudaStreamSynchronize(stream));
+        }
+        return SPH_OK;
+    }
+
+    // Wave-height gauges (Sec. 4.3) on n vertical lines (x, y, z_lo, z_hi).
+    sph_status gauge_height(const double* g, int32_t n, double dz, double* H, int32_t where) override
+    {
+        if (n == 0) return SPH_OK;
+        const bool host = where == SPH_HOST;
+        const size_t b1 = sizeof(double) * (size_t)n;
+        const double* dg = g;
+        double *dH = H, *scratch = nullptr;
+        if (host) {
+            SPH_CUDA(cudaMallocAsync(&scratch, 5 * b1, stream));
+            SPH_CUDA(cudaMemcpyAsync(scratch, g, 4 * b1, cudaMemcpyHostToDevice, stream));
+            dg = scratch;
+            dH = scratch + 4 * (size_t)n;
+        }
+        SPH_KERNEL(SPH_K_OTHER, 1,
+                   k_gauge_height<T><<<(unsigned)n, GAUGE_BLOCK, 0, stream>>>(D_, I_, n, dg, dz, fstart_, pos_[0],
+                                                                             drho_[0], phase_[par_], dH));
+        if (host) {
+            SPH_CUDA(cudaMemcpyAsync(H, dH, b1, cudaMemcpyDeviceToHost, stream));
+            SPH_CUDA(cudaFreeAsync(scratch, stream));
+            SPH_CUDA(cudaStreamSynchronize(stream));
+        }
         return SPH_OK;
     }
 

@@ -64,6 +64,8 @@ class Scene:
     steps: int = 1
     probes: Optional[np.ndarray] = None   # indices into wall_pos
     rho_init: Optional[np.ndarray] = None  # None: hydrostatic initial density
+    sensors: Optional[np.ndarray] = None   # (n, 3) pressure-sensor points
+    gauges: Optional[np.ndarray] = None    # (n, 4) wave-gauge lines x, y, z_lo, z_hi
     dim: int = 3                           # 2: particles in the x-z plane y = 0
 
     @property
@@ -191,6 +193,64 @@ def dam_break(tank: Tuple[float, float, float] = (1.6, 0.67, 0.6),
         fluid_pos=fluid, fluid_vel=np.zeros_like(fluid),
         fluid_phase=np.zeros(fluid.shape[0], np.int32), wall_pos=wall,
         reinit_every=reinit_every, steps=steps, probes=probes)
+
+
+def dam_break_obstacle(tank: Tuple[float, float, float] = (3.0, 1.0, 1.6),
+                       column: Tuple[float, float, float] = (1.0, 1.0, 0.5),
+                       obstacle_lo: Tuple[float, float] = (2.2, 0.3),
+                       obstacle_size: Tuple[float, float, float] = (0.16, 0.4, 0.16),
+                       dp: float = 0.016, layers: int = 3, penalty: bool = True,
+                       reinit_every: int = 1, steps: int = 2000,
+                       roof: bool = False) -> Scene:
+    """3-D dam break onto a box obstacle standing on the bed, with pressure
+    sensors on the obstacle and wave-height gauges along the tank (the
+    configuration of Sec. 4.3; the dimensions here are synthetic).
+
+    A water column (``column``, against the x = 0 wall) in an open box tank
+    whose walls (1.6 m) stand higher than the surge runs up the far wall (a
+    ``roof`` can close it); the obstacle is a solid block of wall particles
+    on the lattice of the tank, from (``obstacle_lo``, z = 0) spanning
+    ``obstacle_size``.  Density reinitialisation every step, as in the
+    paper (Sec. 2.5).  Sensors:
+    four points on the obstacle's upstream face (x = face, y = centre, at
+    1/8, 3/8, 5/8 and 7/8 of its height) and one at the centre of its top.
+    Gauges: vertical lines over the full tank height at x = column/2, column,
+    midway to the obstacle and 0.2 m before it, on the tank's centre line.
+    Defaults at dp = 0.016 m: 123,039 fluid and 179,962 wall particles.
+    """
+    ntx, nty, ntz = (_count(v, dp) for v in tank)
+    ncx, ncy, ncz = (_count(v, dp) for v in column)
+    h = 1.3 * dp
+    H = ncz * dp
+    fluid = lattice((ncx, ncy, ncz), dp)
+    walls = tank_walls((ntx, nty), ntz, dp, layers)
+    ox0, oy0 = _count(obstacle_lo[0], dp), _count(obstacle_lo[1], dp)
+    onx, ony, onz = (_count(v, dp) for v in obstacle_size)
+    if not (ncx < ox0 and ox0 + onx <= ntx and oy0 + ony <= nty and onz < ntz):
+        raise ValueError("the obstacle must stand inside the tank, downstream of the column")
+    block = lattice((onx, ony, onz), dp, origin=(ox0 * dp, oy0 * dp, 0.0))
+    parts = [walls, block]
+    if roof:
+        parts.append(lattice((ntx + 2 * layers, nty + 2 * layers, layers), dp,
+                             origin=(-layers * dp, -layers * dp, ntz * dp)))
+    wall = np.concatenate(parts)
+    lo, hi = _domain(wall, fluid, 2 * h, 0.0 if roof else 0.2)
+    face_x, yc = ox0 * dp, (oy0 + 0.5 * ony) * dp
+    top = onz * dp
+    sensors = np.array([[face_x, yc, f * top] for f in (0.125, 0.375, 0.625, 0.875)]
+                       + [[(ox0 + 0.5 * onx) * dp, yc, top]])
+    Lc, xo = ncx * dp, ox0 * dp
+    gx = (0.5 * Lc, Lc, 0.5 * (Lc + xo), xo - 0.2)
+    gauges = np.array([[x, 0.5 * nty * dp, 0.0, ntz * dp] for x in gx])
+    return Scene(
+        name=(f"dam_break_obstacle_{tank[0]:g}x{tank[1]:g}x{tank[2]:g}"
+              f"_col{column[0]:g}x{column[1]:g}x{column[2]:g}_dp{dp:g}"),
+        dp=dp, h=h, c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G),
+        lo=lo, hi=hi,
+        phases=[Phase(rho0=1000.0, eos="tait", penalty=penalty, z_top=H)],
+        fluid_pos=fluid, fluid_vel=np.zeros_like(fluid),
+        fluid_phase=np.zeros(fluid.shape[0], np.int32), wall_pos=wall,
+        reinit_every=reinit_every, steps=steps, sensors=sensors, gauges=gauges)
 
 
 def two_phase_ramp_cylinder(tank: Tuple[float, float, float] = (1.0, 0.5, 0.5),
@@ -451,6 +511,8 @@ def standard(name: str) -> Scene:
         return dam_break()
     if name == "two_phase_ramp_cylinder":
         return two_phase_ramp_cylinder()
+    if name == "dam_break_obstacle_123k":
+        return dam_break_obstacle()
     if name == "dam_break_adjoint_189k":
         # probes behind the column: the far wall sees no water within 10 steps
         return dam_break(dp=0.0075, steps=10, n_probes=64, probe_wall="near")

@@ -28,7 +28,9 @@ EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_grid_info", "sph_get_cells", "sph_diagnostics", "sph_counters",
            "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_bin_sort_noalloc",
            "sph_profile", "sph_profile_read", "sph_tape", "sph_backward", "sph_step_async",
-           "sph_sync", "sph_diagnostics_async", "sph_set_excitation", "sph_time")
+           "sph_sync", "sph_diagnostics_async", "sph_set_excitation", "sph_time",
+           "sph_probe_pressure", "sph_gauge_height")
+SPH_GAUGE_MAX_SAMPLES = 65536
 SPH_ERR_CAPACITY = 8
 SPH_BIN_SORT_NOALLOC_SCRATCH = 32 << 20
 KERNEL_KINDS = ("begin_step", "predict", "scan", "scatter", "gather", "neighbors",
@@ -120,6 +122,8 @@ def lib() -> C.CDLL:
         L.sph_set_excitation.argtypes = [p, p, d]
         L.sph_time.argtypes = [p, p]
         L.sph_backward.argtypes = [p, p, p, i32]
+        L.sph_probe_pressure.argtypes = [p, p, i32, p, p, i32]
+        L.sph_gauge_height.argtypes = [p, p, i32, d, p, i32]
         for name in EXPORTS:
             if name not in ("sph_last_error", "sph_destroy"):
                 getattr(L, name).restype = st
@@ -264,6 +268,14 @@ def sph_diagnostics_async(ctx, out_ptr: int, where: int = SPH_HOST):
     return lib().sph_diagnostics_async(ctx, out_ptr, int(where))
 
 
+def sph_probe_pressure(ctx, pts_ptr, n: int, p_ptr, w_ptr, where: int = SPH_HOST):
+    return lib().sph_probe_pressure(ctx, pts_ptr, int(n), p_ptr, w_ptr, int(where))
+
+
+def sph_gauge_height(ctx, gauges_ptr, n: int, dz: float, H_ptr, where: int = SPH_HOST):
+    return lib().sph_gauge_height(ctx, gauges_ptr, int(n), float(dz), H_ptr, int(where))
+
+
 def sph_tape(ctx, nsteps: int, dt: float = 0.0):
     last = C.c_double(0.0)
     st = lib().sph_tape(ctx, int(nsteps), float(dt), C.byref(last))
@@ -342,6 +354,24 @@ class Simulation:
         t = C.c_double(0.0)
         _check(lib().sph_time(self.ctx, C.byref(t)), self.ctx)
         return t.value
+
+    def probe_pressure(self, pts):
+        """(p, w) at the points pts (n x 3): the Shepard-interpolated fluid
+        pressure and the kernel sum (sph_probe_pressure)."""
+        q = np.ascontiguousarray(pts, np.float64).reshape(-1, 3)
+        p, w = np.zeros(len(q)), np.zeros(len(q))
+        _check(sph_probe_pressure(self.ctx, _ptr(q), len(q), _ptr(p), _ptr(w)), self.ctx)
+        return p, w
+
+    def gauge_height(self, gauges, dz: Optional[float] = None):
+        """Free-surface height of the first phase on each vertical line
+        (x, y, z_lo, z_hi) of gauges (n x 4), sampled dz apart (default
+        dx/4) (sph_gauge_height)."""
+        g = np.ascontiguousarray(gauges, np.float64).reshape(-1, 4)
+        H = np.zeros(len(g))
+        step = 0.25 * self.scene.dp if dz is None else float(dz)
+        _check(sph_gauge_height(self.ctx, _ptr(g), len(g), step, _ptr(H)), self.ctx)
+        return H
 
     def state(self) -> dict:
         n, m = self.nf, self.nw
