@@ -343,20 +343,33 @@ typedef struct {
 
 /* Advance nsteps steps like sph_step, recording a checkpoint of the state
  * before each step (about 96 bytes per fluid and 24 per wall particle in the
- * FP32 form, twice that in FP64) and the dt used.  Taping must start right
- * after sph_create and continue without untaped steps in between
- * (SPH_ERR_STATE otherwise); nsteps = 0 only records the created state.
- * The checkpoints live until sph_destroy.  Errors: those of sph_step,
- * SPH_ERR_UNSUPPORTED, SPH_ERR_STATE, SPH_ERR_OOM. */
+ * FP32 form, twice that in FP64) and the dt used.  Within the budget set by
+ * sph_tape_budget each step also keeps the products its backward reads:
+ * its neighbour lists and the state after its sweeps (about 1 KB per fluid
+ * and 32 bytes per wall particle in the FP32 form), so that the backward
+ * need not recompute it.  Taping must start right after sph_create and
+ * continue without untaped steps in between (SPH_ERR_STATE otherwise);
+ * nsteps = 0 only records the created state.  Checkpoints and products live
+ * until sph_destroy.  Errors: those of sph_step, SPH_ERR_UNSUPPORTED,
+ * SPH_ERR_STATE, SPH_ERR_OOM. */
 sph_status sph_tape(sph_ctx* ctx, int32_t nsteps, double dt, double* dt_out);
 
-/* Backward sweep over all taped steps, newest first: each step is recomputed
- * from its checkpoint (bit-identical, so the neighbour lists are the
- * forward's), then the adjoint kernels run; finally the sweeps of
- * sph_create at r^0 are differentiated.  The context's state is restored
- * afterwards.  The state must still be the taped run's end (SPH_ERR_STATE
- * after untaped steps).  Synchronises the stream.  Errors: SPH_ERR_ARG,
- * SPH_ERR_STATE, SPH_ERR_OOM, SPH_ERR_CUDA. */
+/* Device memory that sph_tape may spend on keeping step products, in bytes:
+ * -1 (the default) = half the device memory free when the first product is
+ * kept; 0 = keep none (every step is recomputed by the backward).  Steps
+ * beyond the budget are recomputed; the gradients are the same bit for bit
+ * either way.  Takes effect for steps taped afterwards.  Errors: SPH_ERR_ARG
+ * (bytes < -1), SPH_ERR_STATE. */
+sph_status sph_tape_budget(sph_ctx* ctx, int64_t bytes);
+
+/* Backward sweep over all taped steps, newest first: each step's products
+ * are taken from the tape, or the step is recomputed from its checkpoint
+ * (bit-identical, so the neighbour lists are the forward's); then the
+ * adjoint kernels run; finally the sweeps of sph_create at r^0 are
+ * differentiated.  The context's state is restored afterwards.  The state
+ * must still be the taped run's end (SPH_ERR_STATE after untaped steps).
+ * Synchronises the stream.  Errors: SPH_ERR_ARG, SPH_ERR_STATE,
+ * SPH_ERR_OOM, SPH_ERR_CUDA. */
 sph_status sph_backward(sph_ctx* ctx, const sph_adjoint_seed* seed, sph_adjoint_grad* grad,
                         int32_t where);
 

@@ -223,6 +223,17 @@ sph_status sph_time(sph_ctx* ctx, double* t)
     return ctx->sim->time(t);
 }
 
+sph_status sph_tape_budget(sph_ctx* ctx, int64_t bytes)
+{
+    sph_status s = usable(ctx);
+    if (s != SPH_OK) return s;
+    if (bytes < -1) {
+        ctx->sim->err = "bytes must be -1 (half the free memory), 0 (keep none) or a positive budget";
+        return SPH_ERR_ARG;
+    }
+    return ctx->sim->tape_budget(bytes);
+}
+
 sph_status sph_probe_pressure(sph_ctx* ctx, const double* pts, int32_t n, double* p, double* w, int32_t where)
 {
     sph_status s = usable(ctx);

@@ -45,6 +45,7 @@ struct SimBase {
     virtual sph_status profile(uint32_t mask) = 0;
     virtual sph_status profile_read(double* ms, int64_t* timed, int64_t* launches) = 0;
     virtual sph_status tape(int32_t nsteps, double dt, double* dt_out) = 0;
+    virtual sph_status tape_budget(int64_t bytes) = 0;
     virtual sph_status set_excitation(const double amp[3], double freq) = 0;
     virtual sph_status time(double* t) = 0;
     virtual sph_status probe_pressure(const double* pts, int32_t n, double* p, double* w, int32_t where) = 0;

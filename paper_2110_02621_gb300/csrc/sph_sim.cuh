@@ -156,6 +156,9 @@ class Sim final : public SimBase {
         for (cudaGraphExec_t& g : gexec_)
             if (g) cudaGraphExecDestroy(g);
         if (cap_stream_) cudaStreamDestroy(cap_stream_);
+        if (adj_side_) cudaStreamDestroy(adj_side_);
+        for (cudaEvent_t& e : adj_ev_)
+            if (e) cudaEventDestroy(e);
         for (void* p : allocs_) cudaFree(p);
         for (EvPair& e : ev_) {
             cudaEventDestroy(e.a);
@@ -451,7 +454,24 @@ class Sim final : public SimBase {
             }
             Ckpt& c = ck_[(size_t)ntaped_];
             c.reinit = P_.reinit_every > 0 && (steps_ % P_.reinit_every) == 0;
-            sph_status s = prof_mask_ ? one_step(c.reinit) : graph_step(c.reinit);
+            Fwd* f = nullptr;
+            sph_status s = fwd_slot((size_t)ntaped_, f);
+            if (s != SPH_OK) return s;
+            if (f) {
+                // the step writes its neighbour lists straight into the
+                // products (kernel by kernel: a graph holds the live lists)
+                int32_t *lf = nbf_, *lw = nbw_, *lc = ncnt_;
+                nbf_ = f->nbf;
+                nbw_ = f->nbw;
+                ncnt_ = f->ncnt;
+                s = one_step(c.reinit);
+                nbf_ = lf;
+                nbw_ = lw;
+                ncnt_ = lc;
+                if (s == SPH_OK) s = keep_products(*f, c.par);
+            } else {
+                s = prof_mask_ ? one_step(c.reinit) : graph_step(c.reinit);
+            }
             if (s != SPH_OK) return s;
             // the dt the step used, kept on the device for the recompute
             SPH_CUDA(cudaMemcpyAsync(c.dtd, d_dt_, sizeof(T), cudaMemcpyDeviceToDevice, stream));
@@ -463,6 +483,13 @@ class Sim final : public SimBase {
             SPH_CUDA(cudaMemcpyAsync(&ck_[(size_t)k].dt, ck_[(size_t)k].dtd, sizeof(T), cudaMemcpyDeviceToHost,
                                      stream));
         return finish_steps(dt_out);
+    }
+
+    sph_status tape_budget(int64_t bytes) override
+    {
+        fwd_limit_ = bytes;
+        fwd_budget_ = bytes >= 0 ? (size_t)bytes : 0;
+        return SPH_OK;
     }
 
     sph_status backward(const sph_adjoint_seed& seed, sph_adjoint_grad& grad, int32_t where) override
@@ -510,13 +537,31 @@ class Sim final : public SimBase {
 
         for (int64_t k = ntaped_ - 1; k >= 0; --k) {
             const Ckpt& c = ck_[(size_t)k];
-            if ((s = restore(c)) != SPH_OK) return s;
-            // recompute the step bit-identically (same dt, same reinit)
-            SPH_CUDA(cudaMemcpyAsync(d_dt_fixed_, c.dtd, sizeof(T), cudaMemcpyDeviceToDevice, stream));
-            // (momentum's outputs a', v', sigma' are not read by the backward)
-            s = prof_mask_ ? one_step(c.reinit, false) : graph_step(c.reinit, false);
-            if (s != SPH_OK) return s;
+            const Fwd* f = (size_t)k < fwd_.size() && fwd_[(size_t)k].buf ? &fwd_[(size_t)k] : nullptr;
             const int p = c.par, q = p ^ 1;
+            if (!f) {
+                if ((s = restore(c)) != SPH_OK) return s;
+                // recompute the step bit-identically (same dt, same reinit)
+                SPH_CUDA(cudaMemcpyAsync(d_dt_fixed_, c.dtd, sizeof(T), cudaMemcpyDeviceToDevice, stream));
+                // (momentum's outputs a', v', sigma' are not read by the backward)
+                s = prof_mask_ ? one_step(c.reinit, false) : graph_step(c.reinit, false);
+                if (s != SPH_OK) return s;
+            }
+            // the step's products: kept from the tape, or just recomputed
+            const int32_t* fs = f ? f->fstart : fstart_;
+            const int32_t *lf = f ? f->nbf : nbf_, *lw = f ? f->nbw : nbw_, *lc = f ? f->ncnt : ncnt_;
+            const V4<T>* P0 = f ? f->pos0 : pos_[0];
+            const V4<T>* P1 = f ? f->pos1 : pos_[1];
+            const V4<T>* VP = f ? f->velp : vel_[p];
+            const T* R0 = f ? f->drho0 : drho_[0];
+            const T* R1 = f ? f->drho1 : drho_[1];
+            const int4* CQ = f ? f->cellq : cell_[q];
+            const int32_t* IQ = f ? f->idq : id_[q];
+            const V4<T>* WP = f ? f->wpos : wpos_;
+            const V2<T>* WR = f ? f->wrho : wrho_;
+            const int32_t* WT = f ? f->wtag : wtag_;
+            const int32_t* TG = f ? f->tag : d_tag_;
+            const V4<T>* GE = f ? f->geff : d_geff_;
             const int nxt = cur ^ 1;
             const T dt = c.dt;
             if (nf_ > 0) {
@@ -529,25 +574,37 @@ class Sim final : public SimBase {
             if (nw_ > 0)
                 SPH_KERNEL(SPH_K_ADJ_WALL, 1,
                            k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
-                               C_, nw_, fstart_, wpos_, wrho_, wnrm_, wcell_, wtag_, d_tag_, pos_[0], vel_[p], tA_,
-                               gpw_[cur], wc_, adj_param_));
+                               C_, nw_, fs, WP, WR, wnrm_, wcell_, WT, TG, P0, VP, tA_, gpw_[cur], wc_, adj_param_));
+            // The wall continuity adjoint reads only tX of the momentum
+            // adjoint and writes only gpw and the parameter sums, so it runs
+            // beside the fluid continuity adjoint on a side stream (not while
+            // kernels are timed one by one).
+            const bool overlap = adj_side_ && !prof_mask_ && nf_ > 0 && nw_ > 0;
             if (nf_ > 0) {
                 SPH_KERNEL(SPH_K_ADJ_MOMENTUM, 1,
                            k_adj_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
-                               C_, nf_, dt, 0, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_[p], drho_[0],
-                               cell_[q], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], d_geff_, tX_, tV_,
-                               adj_param_));
+                               C_, nf_, dt, 0, fs, wstart_, lf, lw, lc, P0, VP, R0, CQ, WP, WR, wnrm_, wc_, tA_,
+                               gx_[cur], gv_[cur], GE, tX_, tV_, adj_param_));
+                if (overlap) {
+                    SPH_CUDA(cudaEventRecord(adj_ev_[0], stream));
+                    SPH_CUDA(cudaStreamWaitEvent(adj_side_, adj_ev_[0], 0));
+                    k_adj_wall_continuity<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, adj_side_>>>(
+                        C_, nw_, fs, c.wpos, c.wrho, wcell_, WT, TG, P1, VP, R1, tX_, gpw_[nxt], adj_param_);
+                    SPH_LAUNCH();
+                    launches_[SPH_K_ADJ_WALL] += 1;
+                    SPH_CUDA(cudaEventRecord(adj_ev_[1], adj_side_));
+                }
                 SPH_KERNEL(SPH_K_ADJ_CONTINUITY, 1,
                            k_adj_continuity<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
-                               C_, nf_, dt, c.reinit ? 1 : 0, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[1], vel_[p],
-                               drho_[1], cell_[q], c.wpos, c.wrho, tX_, tV_, gx_[cur], id_[q], adj_inv_, c.drho,
-                               c.sigma, gx_[nxt], gv_[nxt], ga_[nxt], adj_param_));
+                               C_, nf_, dt, c.reinit ? 1 : 0, fs, wstart_, lf, lw, lc, P1, VP, R1, CQ, c.wpos,
+                               c.wrho, tX_, tV_, gx_[cur], IQ, adj_inv_, c.drho, c.sigma, gx_[nxt], gv_[nxt],
+                               ga_[nxt], adj_param_));
+                if (overlap) SPH_CUDA(cudaStreamWaitEvent(stream, adj_ev_[1], 0));
             }
-            if (nw_ > 0)
+            if (nw_ > 0 && !overlap)
                 SPH_KERNEL(SPH_K_ADJ_WALL, 1,
                            k_adj_wall_continuity<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
-                               C_, nw_, fstart_, c.wpos, c.wrho, wcell_, wtag_, d_tag_, pos_[1], vel_[p], drho_[1],
-                               tX_, gpw_[nxt], adj_param_));
+                               C_, nw_, fs, c.wpos, c.wrho, wcell_, WT, TG, P1, VP, R1, tX_, gpw_[nxt], adj_param_));
             cur = nxt;
         }
 
@@ -1093,6 +1150,113 @@ class Sim final : public SimBase {
         return SPH_OK;
     }
 
+    // Products of a taped step that its backward reads, kept on the device
+    // while memory allows, so that the reverse sweep need not recompute the
+    // step: the neighbour lists (the step writes them there directly), the
+    // sorted fluid after the continuity sweep (r^{n+1} with p^{n+1}) and as
+    // gathered (r^{n+1} with p^n), v^{n+1/2}, both density excesses, cells and
+    // ids of the new order, the cell ranges, the wall pressures and densities,
+    // the wall support tags with the step's tag, and the body force.
+    struct Fwd {
+        char* buf = nullptr;
+        int32_t *nbf = nullptr, *nbw = nullptr, *ncnt = nullptr;
+        V4<T>*pos0 = nullptr, *pos1 = nullptr, *velp = nullptr, *wpos = nullptr, *geff = nullptr;
+        T *drho0 = nullptr, *drho1 = nullptr;
+        int4* cellq = nullptr;
+        int32_t *idq = nullptr, *fstart = nullptr, *wtag = nullptr, *tag = nullptr;
+        V2<T>* wrho = nullptr;
+    };
+
+    // The products of taped step k: f = &fwd_[k] with its buffer allocated,
+    // or nullptr once the products of the run would pass the budget (by
+    // default half the device memory free when the first one is kept); those
+    // steps are recomputed by the backward.
+    sph_status fwd_slot(size_t k, Fwd*& f)
+    {
+        f = nullptr;
+        if (fwd_.size() <= k) fwd_.resize(k + 1);
+        Fwd& g = fwd_[k];
+        if (g.buf) {
+            f = &g;
+            return SPH_OK;
+        }
+        const size_t nf = (size_t)nf_, nw = (size_t)nw_;
+        size_t off = 0;
+        auto take = [&](size_t bytes) {
+            size_t at = off;
+            off += (bytes + 255) & ~(size_t)255;
+            return at;
+        };
+        const size_t o_nbf = take((size_t)SUBF * LP * nf * sizeof(int32_t)),
+                     o_nbw = take((size_t)SUBW * LP * nf * sizeof(int32_t)),
+                     o_cnt = take((size_t)LP * nf * sizeof(int32_t)), o_p0 = take(nf * sizeof(V4<T>)),
+                     o_p1 = take(nf * sizeof(V4<T>)), o_v = take(nf * sizeof(V4<T>)), o_r0 = take(nf * sizeof(T)),
+                     o_r1 = take(nf * sizeof(T)), o_c = take(nf * sizeof(int4)), o_id = take(nf * sizeof(int32_t)),
+                     o_fs = take(((size_t)n_cells_ + 2) * sizeof(int32_t)), o_wp = take(nw * sizeof(V4<T>)),
+                     o_wr = take(nw * sizeof(V2<T>)), o_wt = take(nw * sizeof(int32_t)),
+                     o_tg = take(sizeof(int32_t)), o_ge = take(sizeof(V4<T>));
+        if (fwd_limit_ < 0 && fwd_budget_ == 0) {
+            size_t fr = 0, tot = 0;
+            SPH_CUDA(cudaMemGetInfo(&fr, &tot));
+            fwd_budget_ = fr / 2 > 1 ? fr / 2 : 1;
+        }
+        if (fwd_bytes_ + off > fwd_budget_) return SPH_OK;
+        sph_status s = alloc(g.buf, off);
+        if (s != SPH_OK) return s;
+        fwd_bytes_ += off;
+        g.nbf = (int32_t*)(g.buf + o_nbf);
+        g.nbw = (int32_t*)(g.buf + o_nbw);
+        g.ncnt = (int32_t*)(g.buf + o_cnt);
+        g.pos0 = (V4<T>*)(g.buf + o_p0);
+        g.pos1 = (V4<T>*)(g.buf + o_p1);
+        g.velp = (V4<T>*)(g.buf + o_v);
+        g.drho0 = (T*)(g.buf + o_r0);
+        g.drho1 = (T*)(g.buf + o_r1);
+        g.cellq = (int4*)(g.buf + o_c);
+        g.idq = (int32_t*)(g.buf + o_id);
+        g.fstart = (int32_t*)(g.buf + o_fs);
+        g.wpos = (V4<T>*)(g.buf + o_wp);
+        g.wrho = (V2<T>*)(g.buf + o_wr);
+        g.wtag = (int32_t*)(g.buf + o_wt);
+        g.tag = (int32_t*)(g.buf + o_tg);
+        g.geff = (V4<T>*)(g.buf + o_ge);
+        f = &g;
+        return SPH_OK;
+    }
+
+    // Copy the products of the step just taken (it started with parity p)
+    // next to its lists, in one launch.
+    sph_status keep_products(Fwd& f, int p)
+    {
+        const size_t nf = (size_t)nf_, nw = (size_t)nw_;
+        const int q = p ^ 1;
+        CopyList L{};
+        auto add = [&](const void* src, void* dst, size_t bytes) {
+            CopySeg& g = L.seg[L.n++];
+            g.dst = dst;
+            g.src = const_cast<void*>(src);
+            g.words = bytes / 4;
+            L.total += g.words;
+        };
+        add(pos_[0], f.pos0, nf * sizeof(V4<T>));
+        add(pos_[1], f.pos1, nf * sizeof(V4<T>));
+        add(vel_[p], f.velp, nf * sizeof(V4<T>));
+        add(drho_[0], f.drho0, nf * sizeof(T));
+        add(drho_[1], f.drho1, nf * sizeof(T));
+        add(cell_[q], f.cellq, nf * sizeof(int4));
+        add(id_[q], f.idq, nf * sizeof(int32_t));
+        add(fstart_, f.fstart, ((size_t)n_cells_ + 2) * sizeof(int32_t));
+        add(wpos_, f.wpos, nw * sizeof(V4<T>));
+        add(wrho_, f.wrho, nw * sizeof(V2<T>));
+        add(wtag_, f.wtag, nw * sizeof(int32_t));
+        add(d_tag_, f.tag, sizeof(int32_t));
+        add(d_geff_, f.geff, sizeof(V4<T>));
+        const int64_t want = (int64_t)((L.total / 4 + 255) / 256);
+        const int nb = (int)(want < 1 ? 1 : (want > 152 * 8 ? 152 * 8 : want));
+        SPH_KERNEL(SPH_K_ADJ_OTHER, 1, k_copy_segments<<<nb, 256, 0, stream>>>(L));
+        return SPH_OK;
+    }
+
     sph_status restore(const Ckpt& c)
     {
         sph_status s = copy_ckpt(c, false);
@@ -1120,6 +1284,8 @@ class Sim final : public SimBase {
         if ((s = alloc(adj_inv_, nf)) != SPH_OK) return s;
         if ((s = alloc(wc_, nw)) != SPH_OK) return s;
         if ((s = alloc(adj_io_, 14 * nf + nw)) != SPH_OK) return s;
+        SPH_CUDA(cudaStreamCreateWithFlags(&adj_side_, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : adj_ev_) SPH_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         return alloc(adj_param_, 3);
     }
 
@@ -1194,6 +1360,11 @@ class Sim final : public SimBase {
     // adjoint: checkpoints (ck_[k] = state before taped step k), snapshot,
     // adjoint state (x, d), (v, sigma), a, p_w in two parities, step temporaries
     std::vector<Ckpt> ck_;
+    std::vector<Fwd> fwd_;  // fwd_[k]: the products of taped step k (buf NULL: recomputed)
+    cudaStream_t adj_side_ = nullptr;  // the backward's second stream and its fork/join events
+    cudaEvent_t adj_ev_[2] = {nullptr, nullptr};
+    size_t fwd_bytes_ = 0, fwd_budget_ = 0;  // bytes kept, and the budget (0: not yet set)
+    int64_t fwd_limit_ = -1;                 // sph_tape_budget: -1 = half the free memory
     Ckpt snap_;
     int64_t ntaped_ = 0, tape_end_ = -1;
     V4<T>*gx_[2] = {nullptr, nullptr}, *gv_[2] = {nullptr, nullptr}, *ga_[2] = {nullptr, nullptr};

@@ -29,7 +29,7 @@ EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_bin_sort_noalloc",
            "sph_profile", "sph_profile_read", "sph_tape", "sph_backward", "sph_step_async",
            "sph_sync", "sph_diagnostics_async", "sph_set_excitation", "sph_time",
-           "sph_probe_pressure", "sph_gauge_height")
+           "sph_probe_pressure", "sph_gauge_height", "sph_tape_budget")
 SPH_GAUGE_MAX_SAMPLES = 65536
 SPH_ERR_CAPACITY = 8
 SPH_BIN_SORT_NOALLOC_SCRATCH = 32 << 20
@@ -123,6 +123,7 @@ def lib() -> C.CDLL:
         L.sph_time.argtypes = [p, p]
         L.sph_backward.argtypes = [p, p, p, i32]
         L.sph_probe_pressure.argtypes = [p, p, i32, p, p, i32]
+        L.sph_tape_budget.argtypes = [p, i64]
         L.sph_gauge_height.argtypes = [p, p, i32, d, p, i32]
         for name in EXPORTS:
             if name not in ("sph_last_error", "sph_destroy"):
@@ -421,6 +422,11 @@ class Simulation:
         _check(st, self.ctx)
         return {k: {"ms": float(ms[i]), "timed": int(timed[i]), "launches": int(launches[i])}
                 for i, k in enumerate(KERNEL_KINDS)}
+
+    def tape_budget(self, nbytes: int):
+        """Device memory the tape may keep step products in (sph_tape_budget;
+        -1 = half the free memory, 0 = recompute every step)."""
+        _check(lib().sph_tape_budget(self.ctx, int(nbytes)), self.ctx)
 
     def tape(self, n: int = 1, dt: float = 0.0) -> float:
         """Advance n steps recording checkpoints for backward()."""
