@@ -192,9 +192,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if it
-    was taken on the current kernel sources."""
+def ncu_traffic(kernel: str, field: str = "dram_bytes_per_launch"):
+    """A per-launch figure of a kernel (DRAM bytes, warp instructions) from the
+    committed ncu summary, if it was taken on the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
@@ -204,7 +204,7 @@ def ncu_traffic(kernel: str):
     entry = rec.get(kernel)
     if not entry or entry.get("source_hash") != kernel_source_hash():
         return None
-    return entry.get("dram_bytes_per_launch")
+    return entry.get(field)
 
 
 def measured_peaks():
@@ -389,6 +389,17 @@ def run_gpu(args):
                     "peak_source": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
                                    f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
                     "flops_per_launch": flops, "ms_per_launch": dom_ms}
+        # the same launch against the SMs' instruction issue rate (4 schedulers
+        # per SM, one warp instruction per cycle each): the bound of an
+        # issue-limited kernel, from ncu's instruction count of the capture
+        inst = ncu_traffic(f"k_{dominant}", "warp_inst_per_launch")
+        if inst:
+            issue_peak = N_SM * 4 * sm_max * 1e6 / 1e12
+            issue = inst / (dom_ms / 1e3) / 1e12
+            roofline["issue"] = {"achieved": issue, "peak": issue_peak, "unit": "T warp-instructions/s",
+                                 "frac": issue / issue_peak,
+                                 "warp_inst_per_launch": inst,
+                                 "source": "smsp__inst_executed.sum of the committed ncu capture"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
