@@ -50,6 +50,13 @@ FLOPS_PAIR = {
     "wall_pressure": 24,    # extrapolation sums
     "neighbors": 11,        # per 27-cell candidate: r (6) and |r|^2 (5)
 }
+# Algorithmic bytes per fluid particle of the streaming kernels (unique state
+# read and written), per cell for the scan, per active wall for the wall
+# pressure (kernel table)
+BYTES_PER_PARTICLE = {"predict": 100, "scatter": 28, "gather": 212, "neighbors": 400, "continuity": 500,
+                      "momentum": 500}
+BYTES_PER_CELL_SCAN = 8
+BYTES_PER_ACTIVE_WALL = 48
 FP32_LANES_PER_SM = 128
 N_SM = 152
 
@@ -207,6 +214,21 @@ def ncu_traffic(kernel: str, field: str = "dram_bytes_per_launch"):
     return entry.get(field)
 
 
+def streaming_roofline(kernel_us: dict, n_fluid: int, n_cells: int, hbm_gbs: float) -> dict:
+    """Achieved HBM bandwidth of the streaming kernels (binning, sort,
+    reorder): algorithmic bytes / live time per step, against the measured
+    copy bandwidth."""
+    out = {}
+    for kind in ("predict", "scan", "scatter", "gather"):
+        us = kernel_us.get(kind, 0.0)
+        if not us:
+            continue
+        b = n_cells * BYTES_PER_CELL_SCAN if kind == "scan" else n_fluid * BYTES_PER_PARTICLE[kind]
+        gbs = b / (us * 1e-6) / 1e9
+        out[kind] = {"bytes": b, "us": us, "GB/s": round(gbs, 1), "frac": round(gbs / hbm_gbs, 4)}
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -232,11 +254,26 @@ def cpu_baseline(sc, active_walls: float, seconds: float):
     steps = n + 1
     total = el + t1
     parts = sc.n_fluid + active_walls
+    cores = oracle.threads()
+    # the same oracle on one core, a shorter sample
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        sim.step(1)
+        t_one = time.perf_counter() - t0
+        n1 = max(1, min(200, int(0.25 * seconds / max(t_one, 1e-3)) - 1))
+        t0 = time.perf_counter()
+        sim.step(n1)
+        total1 = time.perf_counter() - t0 + t_one
+    finally:
+        oracle.set_threads(cores)
     sim.close()
-    return {"value": parts * steps / total / 1e6, "unit": UNIT, "cores": oracle.threads(),
+    return {"value": parts * steps / total / 1e6, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": f"{steps} full steps of the {sc.n_fluid}-fluid/{sc.n_wall}-wall dam break "
-                      f"({total:.1f} s, FP64 C oracle, OpenMP over particles)"}
+                      f"({total:.1f} s, FP64 C oracle, OpenMP over particles)",
+            "single_core": {"value": parts * (n1 + 1) / total1 / 1e6, "unit": UNIT, "cores": 1,
+                            "sample": f"{n1 + 1} further steps ({total1:.1f} s)"}}
 
 
 def run_reference(args):
@@ -358,6 +395,7 @@ def run_gpu(args):
     sim.sync()
     prof2 = sim.profile_read()
     dom_ms = prof2[dominant]["ms"] / max(prof2[dominant]["timed"], 1)
+    _, n_cells, _ = sim.grid()
     sim.close()
 
     parts = sc.n_fluid + active_mean
@@ -401,6 +439,24 @@ def run_gpu(args):
                                  "warp_inst_per_launch": inst,
                                  "source": "smsp__inst_executed.sum of the committed ncu capture"}
 
+    # the whole step against both roofs: its algorithmic flops and bytes give
+    # a lower bound on its time, max(flops / FP32 peak, bytes / HBM peak)
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    step_flops = (cand_tests * FLOPS_PAIR["neighbors"]
+                  + pairs_ff * (FLOPS_PAIR["continuity_ff"] + FLOPS_PAIR["momentum_ff"])
+                  + pairs_fw * (FLOPS_PAIR["continuity_fw"] + FLOPS_PAIR["momentum_fw"]
+                                + FLOPS_PAIR["wall_pressure"]))
+    step_bytes = (sc.n_fluid * sum(BYTES_PER_PARTICLE.values()) + n_cells * BYTES_PER_CELL_SCAN
+                  + active_mean * BYTES_PER_ACTIVE_WALL)
+    t_flops = step_flops / (fp32_peak * 1e12) * 1e6
+    t_bytes = step_bytes / (hbm * 1e9) * 1e6
+    t_step = t_ms / args.steps * 1e3
+    step_roof = {"flops": step_flops, "bytes": step_bytes, "us_at_fp32_peak": t_flops,
+                 "us_at_hbm_peak": t_bytes, "us_measured": t_step,
+                 "frac": max(t_flops, t_bytes) / t_step,
+                 "peaks": f"FP32 {fp32_peak:.1f} TFLOP/s (derived), HBM {hbm:.0f} GB/s (measured copy)"}
+    streaming = streaming_roofline(kernel_us, sc.n_fluid, n_cells, hbm)
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -411,7 +467,8 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "kernel_share_warmup": shares, "kernel_us_per_step_warmup": kernel_us,
                        "step_launch": "one CUDA graph per step"},
-            "roofline": roofline, "gpu_launches": int(launches1 - launches0), "clocks": clk,
+            "roofline": roofline, "step_roofline": step_roof, "streaming_roofline": streaming,
+            "gpu_launches": int(launches1 - launches0), "clocks": clk,
             "host_wall_s": wall1 - wall0}
 
     if rank == 0 and world == 1 and not args.no_e2e:
@@ -596,14 +653,17 @@ def other_workloads(stream, flush, steps: int = 50):
             sim.profile(sph.KERNEL_KINDS)
             sim.step(3)
             prof = sim.profile_read()
+            _, n_cells, _ = sim.grid()
             sim.close()
             active = (a1 - a0) / max(s1 - s0, 1)
+            kus = {k: round(v["ms"] * 1e3 / 3, 1) for k, v in prof.items() if v["timed"]}
             out[name] = {"n_fluid": sc.n_fluid, "n_wall": sc.n_wall, "active_wall_mean": round(active, 1),
                          "ms_per_step": t_ms / steps, "steps": steps,
                          "value": (sc.n_fluid + active) * steps / (t_ms / 1e3) / 1e6,
                          "value_fluid_only": sc.n_fluid * steps / (t_ms / 1e3) / 1e6, "unit": UNIT,
-                         "kernel_us_per_step": {k: round(v["ms"] * 1e3 / 3, 1) for k, v in prof.items()
-                                                if v["timed"]}}
+                         "kernel_us_per_step": kus,
+                         "streaming_roofline": streaming_roofline(
+                             kus, sc.n_fluid, n_cells, float(measured_peaks().get("hbm_gbs", 6800.0)))}
         except Exception as e:  # reported, not fatal: the main line stands on its own
             out[name] = {"error": f"{type(e).__name__}: {e}"}
     return out

@@ -79,6 +79,7 @@ def lib():
             "orc_neighbors": (i64, [p, i64, p, i64, p, p, i64, p]),
             "orc_diagnostics": (None, [p, p]), "orc_sigma0": (d, [p]),
             "orc_step_count": (i64, [p]), "orc_threads": (i32, []),
+            "orc_set_threads": (None, [i32]),
             "orc_set_excitation": (None, [p, p, d]), "orc_time": (d, [p]),
             "orc_probe_pressure": (None, [p, p, i64, p, p]),
             "orc_gauge_height": (None, [p, p, i64, d, p]),
@@ -141,6 +142,11 @@ def riemann(rhoL, UL, pL, rhoR, UR, pR, c, limiter=True):
 
 def lattice_sigma0(dp: float, h: float, dim: int = 3) -> float:
     return lib().orc_lattice_sigma0(dp, h) if dim == 3 else lib().orc_lattice_sigma0_dim(dp, h, dim)
+
+
+def set_threads(n: int):
+    """OpenMP threads the oracle uses from now on."""
+    lib().orc_set_threads(int(n))
 
 
 def threads() -> int:

@@ -174,7 +174,7 @@ def continuity(x, v, rho, p, pw, rhow, P: Params, c0, pairs):
 def wall_pressure(x, rho, p, P: Params, c0, wpairs, nw):
     """Eq. (wallPressure), fixed walls, rho_f weighting the g term:
     p_w = sum_f (p_f + rho_f g.r_wf) W_wf / sum_f W_wf, r_wf = r_w - r_f;
-    no support: p_w = 0.  rho_w = EOS^-1(p_w)."""
+    no support: p_w = 0.  rho_w = EOS^-1(p_w), at least rho0/2."""
     wi, ww = wpairs
     rwf = P.xw[ww] - x[wi]
     r = torch.sqrt((rwf * rwf).sum(dim=1))
@@ -183,7 +183,9 @@ def wall_pressure(x, rho, p, P: Params, c0, wpairs, nw):
     den = torch.zeros(nw, dtype=F64).index_add(0, ww, Wk)
     has = den > 0.0
     pw = torch.where(has, num / torch.where(has, den, torch.ones_like(den)), torch.zeros_like(den))
-    return pw, eos_rho(pw, P, c0)
+    # rho_w kept at or above rho0/2: EOS^-1 of max(p_w, EOS(rho0/2))
+    p_half = eos_p(0.5 * P.rho0 * torch.ones_like(pw), P, c0)
+    return pw, eos_rho(torch.maximum(pw, p_half), P, c0)
 
 
 def momentum(x, v, rho, p, pw, rhow, P: Params, c0, gamma_p, mu, pairs):

@@ -15,7 +15,10 @@
  *     rho_f, which makes the printed expression dimensionally consistent;
  *     multi-phase weights are W/rho_f (the "divided by rho_f" of Sec. 2.3);
  *   - wall mass m_w = rho^0 dx^3 of the interacting fluid particle's phase,
- *     wall density rho_w from the inverse equation of state of that phase;
+ *     wall density rho_w from the inverse equation of state of that phase,
+ *     kept at or above rho^0/2 (below EOS(rho^0/2) the Tait inverse nears
+ *     the edge of its domain p > -rho^0 c^2/gamma, and extrapolations that
+ *     average fluid torn to half its density pass it);
  *     walls have zero velocity;
  *   - penalty (Eq. penaltyMethodTerm): delta = 2 |(r_i - r_w).n_w| / dx,
  *     the distance of i from the wall particle's tangent plane in units of
@@ -332,7 +335,11 @@ static void wall_pressure(orc_sim* s)
         s->pw[w] = pw;
         for (int k = 0; k < 2; k++) {
             int kk = k < s->P.n_phases ? k : 0;
-            s->rhow[2 * w + k] = orc_eos_rho(pw, &s->P.phase[kk], s->P.c0, s->P.gamma_tait);
+            const orc_phase* ph = &s->P.phase[kk];
+            /* rho_w = EOS^-1(p_w), kept at or above rho0/2 */
+            double p_half = orc_eos_p(0.5 * ph->rho0, ph, s->P.c0, s->P.gamma_tait);
+            s->rhow[2 * w + k] = pw < p_half ? 0.5 * ph->rho0
+                                             : orc_eos_rho(pw, ph, s->P.c0, s->P.gamma_tait);
         }
     }
 }
@@ -861,6 +868,15 @@ int32_t orc_threads(void)
     return (int32_t)omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+void orc_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads((int)n);
+#else
+    (void)n;
 #endif
 }
 

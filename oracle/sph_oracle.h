@@ -99,6 +99,7 @@ void orc_diagnostics(const orc_sim* s, double out[8]);
 double orc_sigma0(const orc_sim* s);
 int64_t orc_step_count(const orc_sim* s);
 int32_t orc_threads(void);
+void orc_set_threads(int32_t n); /* OpenMP threads of the following calls */
 /* sensors (Sec. 4.3): Shepard-interpolated pressure p_bar and kernel sum w at
  * n points pts[3k..3k+2]; either output may be NULL */
 void orc_probe_pressure(const orc_sim* s, const double* pts, int64_t n,

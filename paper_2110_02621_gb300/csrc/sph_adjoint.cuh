@@ -279,7 +279,8 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
             T out = T(0);
             if (live && den > T(0)) {
                 const T dw = rho_w - P.rho0;
-                const T dd_dp = T(1) / eos_dp_dd(P, C, dw, pw.w);
+                // rho_w held at rho0/2 below p_half does not move with p_w or c0
+                const T dd_dp = pw.w < P.p_half ? T(0) : T(1) / eos_dp_dd(P, C, dw, pw.w);
                 const T pbar = gpw_in[w] + Gp + Gr * dd_dp;
                 gc0 = (double)(Gr * (T(-2) * pw.w * C.inv_c0 * dd_dp));
                 out = pbar / den;
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_continuity(
         if (t % LP == 0) {
             T out = T(0);
             if (live) {
-                const T dd_dp = T(1) / eos_dp_dd(P, C, rho_w - P.rho0, pw.w);
+                const T dd_dp = pw.w < P.p_half ? T(0) : T(1) / eos_dp_dd(P, C, rho_w - P.rho0, pw.w);
                 out = Gp + Gr * dd_dp;
                 Gc = Gr * (T(-2) * pw.w * C.inv_c0 * dd_dp);
             }

@@ -28,6 +28,7 @@ struct PhaseK {
     T mu;               // dynamic viscosity
     T m;                // particle mass rho0 dx^3 (also the wall mass seen by this phase)
     T eos_k;            // Tait: rho0 c^2 / gamma; linear: c^2
+    T p_half;           // EOS(rho0 / 2): wall densities are kept at or above rho0 / 2
     int32_t eos, density, reinit, penalty;
 };
 

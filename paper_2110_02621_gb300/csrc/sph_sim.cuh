@@ -137,6 +137,9 @@ Cfg<T> make_cfg(const sph_params& P, const int32_t dims[3])
         q.mu = (T)ph.mu;
         q.m = (T)(ph.rho0 * vol);
         q.eos_k = ph.eos == SPH_EOS_TAIT ? (T)(ph.rho0 * P.c0 * P.c0 / P.gamma_tait) : (T)(P.c0 * P.c0);
+        q.p_half = ph.eos == SPH_EOS_TAIT
+                       ? (T)(ph.rho0 * P.c0 * P.c0 / P.gamma_tait * (std::pow(0.5, P.gamma_tait) - 1.0))
+                       : (T)(-0.5 * ph.rho0 * P.c0 * P.c0);
         q.eos = ph.eos;
         q.density = ph.density;
         q.reinit = ph.reinit;

@@ -384,13 +384,23 @@ __global__ void __launch_bounds__(LBLOCK) k_continuity(
 }
 
 // ----------------------------------------------------------- wall pressure
+// Wall dummy density of a phase from the wall pressure, rho_w = EOS^-1(p_w)
+// (Sec. 2.3), kept at or above rho0/2: below EOS(rho0/2) -- reached only
+// where the extrapolation averages fluid torn to half its density -- the
+// inverse would approach (Tait: leave) the edge of its domain, p > -rho0 c^2/gamma.
+template <class T>
+__device__ __forceinline__ T wall_density(const PhaseK<T>& P, const Cfg<T>& C, T p_w)
+{
+    return p_w < P.p_half ? T(0.5) * P.rho0 : P.rho0 + eos_drho(P, C, p_w);
+}
+
 // Eq. (wallPressure) with fixed walls (a_w = 0), reading the (g - a_w) term
 // with the fluid density (dimensionally consistent form):
 //   p_w = sum_f (p_f + rho_f g.r_wf) w_wf / sum_f w_wf,  r_wf = r_w - r_f,
 // w = W (one phase) or W/rho_f (several phases, Sec. 2.3).  Walls without
 // fluid support (not tagged by this step's neighbour build) get p_w = 0 and
 // rho_w = rho0 at once; the others split the fluid of their 27 cells over LP
-// lanes.  rho_w = rho0 + EOS^-1(p_w) per phase.
+// lanes.  rho_w = rho0 + EOS^-1(p_w) per phase, at least rho0/2.
 template <class T>
 __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
     Cfg<T> C, int32_t nw, const int32_t* __restrict__ fstart, V4<T>* __restrict__ wpos,
@@ -423,8 +433,8 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
             const T p_w = den > T(0) ? num / den : T(0);
             has = den > T(0);
             reinterpret_cast<T*>(wpos + w)[3] = p_w;
-            const T r0 = C.ph[0].rho0 + eos_drho(C.ph[0], C, p_w);
-            const T r1 = multi ? C.ph[1].rho0 + eos_drho(C.ph[1], C, p_w) : r0;
+            const T r0 = wall_density(C.ph[0], C, p_w);
+            const T r1 = multi ? wall_density(C.ph[1], C, p_w) : r0;
             wrho[w] = V2<T>{r0, r1};
         }
     }

@@ -448,6 +448,32 @@ def test_2d_parity(make, tol):
         check_state(sim.state(), ref2.fluid(), ref2.wall(), sc.dp, tol_rate=1e-7, tol_x=1e-9, what="fp64")
 
 
+@pytest.mark.parametrize("eos", ["tait", "linear"])
+@pytest.mark.parametrize("precision", [sph.SPH_FP32, sph.SPH_FP64_PLAIN])
+def test_wall_density_floor(eos, precision):
+    """A fluid particle torn to 0.3 rho0 under a roof: the extrapolated wall
+    pressure falls below EOS(rho0/2) (for Tait, below the inverse EOS's
+    domain) and the wall density is held at rho0/2; the run stays finite and
+    follows the oracle."""
+    from test_oracle_pins import torn_fluid_under_a_roof
+    sc, rho = torn_fluid_under_a_roof(eos)
+    ref = oracle.OracleSim(sc, rho=rho)
+    sim = sph.Simulation(sc, precision=precision, rho=rho)
+    g, ow = sim.state(), ref.wall()
+    assert np.array_equal(g["rhow"][:, 0] == 500.0, ow["rhow"][:, 0] == 500.0)
+    assert (ow["rhow"][:, 0] == 500.0).any()
+    tol = 1e-5 if precision == sph.SPH_FP32 else 1e-12
+    assert np.allclose(g["rhow"], ow["rhow"], rtol=tol)
+    assert rel_inf(g["pw"], ow["pw"]) <= tol
+    ref.step(5, 1e-5)
+    sim.step(5, 1e-5)
+    g, o = sim.state(), ref.fluid()
+    assert np.all(np.isfinite(g["v"])) and np.all(np.isfinite(g["a"]))
+    assert np.abs(g["x"] - o["x"]).max() <= 1e-6 * sc.dp
+    assert rel_inf(g["a"], o["a"]) <= (2e-5 if precision == sph.SPH_FP32 else 1e-9)
+    sim.close()
+
+
 def test_2d_input_checks():
     sc = S.dam_break_2d(dx=0.01)
     sc.fluid_pos = sc.fluid_pos.copy()

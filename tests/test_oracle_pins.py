@@ -233,6 +233,46 @@ def test_wall_pressure_hydrostatic_extrapolation():
     assert np.max(np.abs(pw[has] - expect)) < 1e-6 * 1000 * G * H
 
 
+def torn_fluid_under_a_roof(eos="tait"):
+    """One fluid particle torn to 0.3 rho0 (tension near the Tait limit) 0.01 m
+    below a 3 x 3 patch of roof wall particles: the extrapolated p_w of the wall
+    above it is p_f + rho_f g.r_wf = p_f - 0.3 rho0 g dz, below EOS(rho0/2)."""
+    dp = 0.01
+    xw = np.array([[i * dp, j * dp, dp] for i in (-1, 0, 1) for j in (-1, 0, 1)])
+    sc = S.Scene(name="torn", dp=dp, h=1.3 * dp, c0=10.0, g=(0.0, 0.0, -G), lo=(-0.1, -0.1, -0.1),
+                 hi=(0.1, 0.1, 0.1), phases=[S.Phase(rho0=1000.0, eos=eos, z_top=0.0)],
+                 fluid_pos=np.zeros((1, 3)), fluid_vel=np.zeros((1, 3)),
+                 fluid_phase=np.zeros(1, np.int32), wall_pos=xw)
+    return sc, np.array([300.0])
+
+
+@pytest.mark.parametrize("eos", ["tait", "linear"])
+def test_wall_density_is_kept_at_half_the_reference(eos):
+    """Below EOS(rho0/2) the wall density is rho0/2 (the Tait inverse has no
+    value below -rho0 c^2/gamma: a NaN there stops the run); above it, the
+    inverse EOS.  Pinned by the closed forms of both equations of state."""
+    sc, rho = torn_fluid_under_a_roof(eos)
+    o = oracle.OracleSim(sc, rho=rho)
+    w = o.wall()
+    ph = sc.phases[0]
+    p_f = oracle.eos_p(300.0, ph, sc.c0)
+    B = 1000.0 * sc.c0 ** 2 / (7.0 if eos == "tait" else 1.0)
+    assert p_f == pytest.approx(B * (0.3 ** 7 - 1.0) if eos == "tait" else -700.0 * sc.c0 ** 2, rel=1e-12)
+    centre = 4  # the wall right above the particle
+    assert w["pw"][centre] == pytest.approx(p_f - 300.0 * G * 0.01, rel=1e-12)
+    p_half = B * (0.5 ** 7 - 1.0) if eos == "tait" else -500.0 * sc.c0 ** 2
+    for k in range(9):
+        if w["pw"][k] < p_half:
+            assert w["rhow"][k, 0] == 500.0
+        else:
+            assert w["rhow"][k, 0] == pytest.approx(oracle.eos_rho(w["pw"][k], ph, sc.c0), rel=1e-13)
+    if eos == "tait":
+        assert w["pw"][centre] < -B < p_half  # the inverse EOS would be NaN here
+    o.step(5, 1e-5)
+    f = o.fluid()
+    assert np.all(np.isfinite(f["x"])) and np.all(np.isfinite(f["v"])) and np.all(np.isfinite(f["rho"]))
+
+
 # -------------------------------------------------------------- continuity
 def test_continuity_galilean_and_rest():
     """Uniform density and velocity: d rho/dt = 0; with non-uniform density the
