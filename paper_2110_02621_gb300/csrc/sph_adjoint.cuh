@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
     T* __restrict__ wc, double* gparam)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int w = t / LP;
+    const int w = t / AWLP;
     double gc0 = 0.0;
     if (w < nw) {
         const PhaseK<T>& P = C.ph[0];
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
         if (live) {
             const V4<T> nn = wnrm[w];
             const int4 c = wcell[w];
-            scan_compact(C, c, pw, fstart, pos, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact<AWLP>(C, c, pw, fstart, pos, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 // scan vector is x_w - x_f; the pair vector of the fluid is x_f - x_w
                 const V4<T> pf = pos[j], vf = vel[j], Aj = tA[j];
                 WallMomAdj<T> o;
@@ -271,11 +271,11 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
                 Gr += o.rho_w;
                 den += kernel_W(C, r2 * p_rsqrt(r2));
             });
-            Gp = group_sum(Gp);
-            Gr = group_sum(Gr);
-            den = group_sum(den);
+            Gp = group_sum<AWLP>(Gp);
+            Gr = group_sum<AWLP>(Gr);
+            den = group_sum<AWLP>(den);
         }
-        if (t % LP == 0) {
+        if (t % AWLP == 0) {
             T out = T(0);
             if (live && den > T(0)) {
                 const T dw = rho_w - P.rho0;
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_continuity(
     const T* __restrict__ drho1, const V4<T>* __restrict__ tX, T* __restrict__ gpw_out, double* gparam)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int w = t / LP;
+    const int w = t / AWLP;
     double gc0 = 0.0;
     if (w < nw) {
         const PhaseK<T>& P = C.ph[0];
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_continuity(
         T Gp = T(0), Gr = T(0), Gc = T(0);
         if (live) {
             const int4 c = wcell[w];
-            scan_compact(C, c, pw, fstart, pos1, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact<AWLP>(C, c, pw, fstart, pos1, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 const V4<T> pf = pos1[j], vf = vel[j];
                 WallContAdj<T> o;
                 wall_continuity_adj(C, P, -rx, -ry, -rz, r2, vf.x, vf.y, vf.z, P.rho0 + drho1[j], pf.w, rho_w,
@@ -595,10 +595,10 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_continuity(
                 Gp += o.p_w;
                 Gr += o.rho_w;
             });
-            Gp = group_sum(Gp);
-            Gr = group_sum(Gr);
+            Gp = group_sum<AWLP>(Gp);
+            Gr = group_sum<AWLP>(Gr);
         }
-        if (t % LP == 0) {
+        if (t % AWLP == 0) {
             T out = T(0);
             if (live) {
                 const T dd_dp = pw.w < P.p_half ? T(0) : T(1) / eos_dp_dd(P, C, rho_w - P.rho0, pw.w);

@@ -576,7 +576,7 @@ class Sim final : public SimBase {
             }
             if (nw_ > 0)
                 SPH_KERNEL(SPH_K_ADJ_WALL, 1,
-                           k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
+                           k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
                                C_, nw_, fs, WP, WR, wnrm_, wcell_, WT, TG, P0, VP, tA_, gpw_[cur], wc_, adj_param_));
             // The wall continuity adjoint reads only tX of the momentum
             // adjoint and writes only gpw and the parameter sums, so it runs
@@ -591,7 +591,7 @@ class Sim final : public SimBase {
                 if (overlap) {
                     SPH_CUDA(cudaEventRecord(adj_ev_[0], stream));
                     SPH_CUDA(cudaStreamWaitEvent(adj_side_, adj_ev_[0], 0));
-                    k_adj_wall_continuity<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, adj_side_>>>(
+                    k_adj_wall_continuity<T><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, adj_side_>>>(
                         C_, nw_, fs, c.wpos, c.wrho, wcell_, WT, TG, P1, VP, R1, tX_, gpw_[nxt], adj_param_);
                     SPH_LAUNCH();
                     launches_[SPH_K_ADJ_WALL] += 1;
@@ -606,7 +606,7 @@ class Sim final : public SimBase {
             }
             if (nw_ > 0 && !overlap)
                 SPH_KERNEL(SPH_K_ADJ_WALL, 1,
-                           k_adj_wall_continuity<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
+                           k_adj_wall_continuity<T><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
                                C_, nw_, fs, c.wpos, c.wrho, wcell_, WT, TG, P1, VP, R1, tX_, gpw_[nxt], adj_param_));
             cur = nxt;
         }
@@ -621,7 +621,7 @@ class Sim final : public SimBase {
                        k_adj_prep<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, T(0), gv_[cur], ga_[cur], tA_));
         if (nw_ > 0)
             SPH_KERNEL(SPH_K_ADJ_WALL, 1,
-                       k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(
+                       k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
                            C_, nw_, fstart_, wpos_, wrho_, wnrm_, wcell_, wtag_, d_tag_, pos_[0], vel_[p0], tA_,
                            gpw_[cur], wc_, adj_param_));
         if (nf_ > 0) {
@@ -947,7 +947,7 @@ class Sim final : public SimBase {
     {
         if (nw_ == 0) return SPH_OK;
         SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
-                   k_wall_pressure<T><<<grid_for((int64_t)nw_ * LP), BLOCK, 0, stream>>>(C_, nw_, fstart_, wpos_,
+                   k_wall_pressure<T><<<grid_for((int64_t)nw_ * WLP), BLOCK, 0, stream>>>(C_, nw_, fstart_, wpos_,
                                                                                          wcell_, pos_[0],
                                                                            vel_cur, wrho_, wtag_, d_tag_,
                                                                            d_geff_, d_active_));

@@ -26,9 +26,11 @@
 
 namespace sph {
 
-constexpr int LP = 4;        // lanes per target particle
-constexpr int SUBF = 40;     // fluid entries per lane sub-list (about 80/LP used)
-constexpr int SUBW = 16;     // wall entries per lane sub-list
+constexpr int LP = 2;        // lanes per target particle
+constexpr int SUBF = 80;     // fluid entries per lane sub-list (about 80/LP used)
+constexpr int SUBW = 32;     // wall entries per lane sub-list
+constexpr int WLP = 8;       // lanes per wall particle in the wall-pressure sweep
+constexpr int AWLP = 4;      // lanes per wall particle in the adjoint's wall sweeps
 constexpr int LBLOCK = 128;  // threads per block
 
 __device__ __forceinline__ int code_of(int dx, int dy, int dz) { return (dx + 1) | (dy + 1) << 2 | (dz + 1) << 4; }
@@ -67,31 +69,33 @@ __device__ __forceinline__ T minus_ref(T s, T c, T ref_hi, T ref_lo)
     return (s - ref_hi) - (c + ref_lo);
 }
 
-// The LP lanes of a particle always take the same path (everything they
-// branch on is per particle), while different groups of a warp may not: the
-// group shuffles therefore name only the group's own lanes.
+// The G lanes of a particle (G = LP, WLP or AWLP for wall particles)
+// always take the same path (everything they branch on is per particle),
+// while different groups of a warp may not: the group shuffles therefore
+// name only the group's own lanes.
+template <int G = LP>
 __device__ __forceinline__ unsigned group_mask()
 {
-    return ((1u << LP) - 1u) << ((threadIdx.x & 31) & ~(LP - 1));
+    return ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
 }
 
-// sum over the LP lanes of a group (fixed tree: deterministic)
-template <class T>
+// sum over the G lanes of a group (fixed tree: deterministic)
+template <int G = LP, class T>
 __device__ __forceinline__ T group_sum(T v)
 {
-    const unsigned m = group_mask();
-    for (int o = LP / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o, LP);
+    const unsigned m = group_mask<G>();
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(m, v, o, G);
     return v;
 }
 
-// merge the compensated sums (s - c) of the LP lanes (TwoSum of the s parts)
-template <class T>
+// merge the compensated sums (s - c) of the G lanes (TwoSum of the s parts)
+template <int G = LP, class T>
 __device__ __forceinline__ void group_kahan(T& s, T& c)
 {
-    const unsigned m = group_mask();
-    for (int o = LP / 2; o > 0; o >>= 1) {
-        const T s2 = __shfl_xor_sync(m, s, o, LP);
-        const T c2 = __shfl_xor_sync(m, c, o, LP);
+    const unsigned m = group_mask<G>();
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const T s2 = __shfl_xor_sync(m, s, o, G);
+        const T c2 = __shfl_xor_sync(m, c, o, G);
         const T t = s + s2;
         const T bp = t - s;
         const T err = (s - (t - bp)) + (s2 - bp);  // s + s2 = t + err exactly
@@ -183,10 +187,11 @@ __device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const 
 }
 
 // The same candidates as scan_share in a compact loop (one loop per row, the
-// x shift chosen per candidate, no unrolling): for the rare fall-back scans of
-// over-full sub-lists and for the per-wall kernels, where code size and
-// registers matter more than the last instruction per candidate.
-template <class T, class Fn>
+// x shift chosen per candidate, no unrolling), lane l of NL taking every NL-th
+// candidate: for the rare fall-back scans of over-full sub-lists and for the
+// per-wall kernels, where code size and registers matter more than the last
+// instruction per candidate.
+template <int NL = LP, class T, class Fn>
 __device__ __forceinline__ void scan_compact(const Cfg<T>& C, const int4& c, const V4<T>& o,
                                              const int32_t* __restrict__ start, const V4<T>* __restrict__ pts,
                                              int l, Fn&& fn)
@@ -207,7 +212,7 @@ __device__ __forceinline__ void scan_compact(const Cfg<T>& C, const int4& c, con
             const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
             const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
 #pragma unroll 1
-            for (int j = b + l; j < e; j += LP) {
+            for (int j = b + l; j < e; j += NL) {
                 const V4<T> pj = pts[j];
                 const int dxc = j < b1 ? 0 : (j < b2 ? 1 : 2);  // dx + 1
                 const T rx = (dxc == 0 ? xl : (dxc == 1 ? o.x : xr)) - pj.x;
@@ -399,7 +404,7 @@ __device__ __forceinline__ T wall_density(const PhaseK<T>& P, const Cfg<T>& C, T
 //   p_w = sum_f (p_f + rho_f g.r_wf) w_wf / sum_f w_wf,  r_wf = r_w - r_f,
 // w = W (one phase) or W/rho_f (several phases, Sec. 2.3).  Walls without
 // fluid support (not tagged by this step's neighbour build) get p_w = 0 and
-// rho_w = rho0 at once; the others split the fluid of their 27 cells over LP
+// rho_w = rho0 at once; the others split the fluid of their 27 cells over WLP
 // lanes.  rho_w = rho0 + EOS^-1(p_w) per phase, at least rho0/2.
 template <class T>
 __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
@@ -409,7 +414,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
     const V4<T>* __restrict__ geff, unsigned long long* active)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int w = t / LP;
+    const int w = t / WLP;
     int has = 0;
     if (w < nw) {
         const bool multi = C.n_phases > 1;
@@ -418,7 +423,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
             const V4<T> ge = *geff;
             const int4 c = wcell[w];
             const V4<T> pw = wpos[w];
-            scan_compact(C, c, pw, fstart, pos, t % LP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact<WLP>(C, c, pw, fstart, pos, t % WLP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 const T W = kernel_W(C, r2 * p_rsqrt(r2));
                 const T p_f = reinterpret_cast<const T*>(pos + j)[3];
                 const T rho_f = vel[j].w;
@@ -426,10 +431,10 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
                 num += (p_f + rho_f * (ge.x * rx + ge.y * ry + ge.z * rz)) * om;
                 den += om;
             });
-            num = group_sum(num);
-            den = group_sum(den);
+            num = group_sum<WLP>(num);
+            den = group_sum<WLP>(den);
         }
-        if (t % LP == 0) {
+        if (t % WLP == 0) {
             const T p_w = den > T(0) ? num / den : T(0);
             has = den > T(0);
             reinterpret_cast<T*>(wpos + w)[3] = p_w;
@@ -481,9 +486,7 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
             const bool sig_all = P.density == 1;
             const T rho_i = vi.w, p_i = pi.w, pr_i = p_div(p_i, rho_i), mu_i = P.mu;
             T ax = T(0), ay = T(0), az = T(0), sg = lead ? C.W0 : T(0), se = T(0);
-            for_neighbors(
-                C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
-                [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
+            auto fluid_pair = [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
                     const V4<T> vj = vel[j];
                     const T rinv = p_rsqrt(r2);
                     const T r = r2 * rinv;
@@ -507,8 +510,8 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
                     ay += k * ry;
                     az += k * rz;
                     if (sig_all || phj == ph) kahan_add(sg, se, W);
-                },
-                [&](int w, const V4<T>& pw, T rx, T ry, T rz, T r2) {
+                };
+            auto wall_pair = [&](int w, const V4<T>& pw, T rx, T ry, T rz, T r2) {
                     const V2<T> rw = wrho[w];
                     const T rho_w = ph == 0 ? rw.x : rw.y;
                     const T rinv = p_rsqrt(r2);
@@ -541,7 +544,8 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
                         }
                     }
                     kahan_add(sg, se, W);
-                });
+                };
+            for_neighbors(C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos, fluid_pair, wall_pair);
             const V4<T> ge = *geff;
             ax = group_sum(ax) + ge.x;
             ay = group_sum(ay) + ge.y;
