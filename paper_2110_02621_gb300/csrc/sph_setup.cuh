@@ -246,13 +246,15 @@ __global__ void k_diag_partial(Cfg<T> C, InitCfg I, int32_t n, const V4<T>* __re
                                const V4<T>* __restrict__ vel, const int4* __restrict__ cell,
                                const int32_t* __restrict__ phase, double* __restrict__ partial)
 {
-    __shared__ double sh[8][BLOCK];
+    __shared__ double sh[8][BLOCK / 32];
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (k < n) {
         V4<T> p = pos[k], v = vel[k];
         int4 c = cell[k];
-        double m = (double)C.ph[phase[k]].m;
+        // the phase picked by value: an indexed kernel parameter would go
+        // through local memory
+        double m = (double)(phase[k] == 0 ? C.ph[0].m : C.ph[1].m);
         double vx = v.x, vy = v.y, vz = v.z;
         double x = I.lo[0] + (double)c.x * I.cs + (double)p.x;
         double y = I.lo[1] + (double)c.y * I.cs + (double)p.y;
@@ -266,29 +268,52 @@ __global__ void k_diag_partial(Cfg<T> C, InitCfg I, int32_t n, const V4<T>* __re
         q[6] = c.w >= 0 ? sqrt(vx * vx + vy * vy + vz * vz) : 0.0;
         q[7] = c.w >= 0 ? 0.0 : 1.0;
     }
-    for (int f = 0; f < 8; ++f) sh[f][threadIdx.x] = q[f];
+    // fixed trees (deterministic): xor shuffles in each warp, then the warps
+    for (int o = 16; o > 0; o >>= 1)
+        for (int f = 0; f < 8; ++f) {
+            const double y = __shfl_xor_sync(0xffffffffu, q[f], o);
+            q[f] = f == 6 ? fmax(q[f], y) : q[f] + y;
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int f = 0; f < 8; ++f) sh[f][threadIdx.x >> 5] = q[f];
     __syncthreads();
-    for (int s = BLOCK / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s)
-            for (int f = 0; f < 8; ++f)
-                sh[f][threadIdx.x] = f == 6 ? fmax(sh[f][threadIdx.x], sh[f][threadIdx.x + s])
-                                            : sh[f][threadIdx.x] + sh[f][threadIdx.x + s];
-        __syncthreads();
+    if (threadIdx.x < 8) {
+        const int f = threadIdx.x;
+        double a = sh[f][0];
+        for (int w = 1; w < BLOCK / 32; ++w) a = f == 6 ? fmax(a, sh[f][w]) : a + sh[f][w];
+        partial[blockIdx.x * 8 + f] = a;
     }
-    if (threadIdx.x < 8) partial[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-static __global__ void k_diag_final(int32_t nblocks, const double* __restrict__ partial,
-                                    double* __restrict__ out)
+// The 8 sums over the blocks' partials: DIAG_THREADS threads stride over the
+// blocks for each quantity, then a fixed tree combines them (deterministic).
+constexpr int DIAG_THREADS = 256;
+
+static __global__ void __launch_bounds__(DIAG_THREADS) k_diag_final(int32_t nblocks,
+                                                                    const double* __restrict__ partial,
+                                                                    double* __restrict__ out)
 {
-    if (threadIdx.x >= 8) return;
-    int f = threadIdx.x;
-    double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-        double v = partial[b * 8 + f];
-        s = f == 6 ? fmax(s, v) : s + v;
+    __shared__ double sh[8][DIAG_THREADS / 32];
+    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < nblocks; b += DIAG_THREADS)
+        for (int f = 0; f < 8; ++f) {
+            const double v = partial[b * 8 + f];
+            q[f] = f == 6 ? fmax(q[f], v) : q[f] + v;
+        }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int f = 0; f < 8; ++f) {
+            const double y = __shfl_xor_sync(0xffffffffu, q[f], o);
+            q[f] = f == 6 ? fmax(q[f], y) : q[f] + y;
+        }
+    if ((threadIdx.x & 31) == 0)
+        for (int f = 0; f < 8; ++f) sh[f][threadIdx.x >> 5] = q[f];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int f = threadIdx.x;
+        double a = sh[f][0];
+        for (int w = 1; w < DIAG_THREADS / 32; ++w) a = f == 6 ? fmax(a, sh[f][w]) : a + sh[f][w];
+        out[f] = a;
     }
-    out[f] = s;
 }
 
 }  // namespace sph

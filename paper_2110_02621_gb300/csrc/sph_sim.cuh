@@ -770,7 +770,7 @@ class Sim final : public SimBase {
         SPH_KERNEL(SPH_K_OTHER, 1,
                    k_diag_partial<T><<<nb, BLOCK, 0, stream>>>(C_, I_, nf_, pos_[0], vel_[par_], cell_[par_],
                                                                phase_[par_], diag_partial_));
-        SPH_KERNEL(SPH_K_OTHER, 1, k_diag_final<<<1, 32, 0, stream>>>(nb, diag_partial_, diag_out_));
+        SPH_KERNEL(SPH_K_OTHER, 1, k_diag_final<<<1, DIAG_THREADS, 0, stream>>>(nb, diag_partial_, diag_out_));
         SPH_CUDA(cudaMemcpyAsync(out, diag_out_, sizeof(double) * 8,
                                  where == SPH_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, stream));
         return SPH_OK;
