@@ -26,9 +26,9 @@
 
 namespace sph {
 
-constexpr int LP = 2;        // lanes per target particle
-constexpr int SUBF = 80;     // fluid entries per lane sub-list (about 80/LP used)
-constexpr int SUBW = 32;     // wall entries per lane sub-list
+constexpr int LP = 4;        // lanes per target particle
+constexpr int SUBF = 40;     // fluid entries per lane sub-list (about 80/LP used)
+constexpr int SUBW = 16;     // wall entries per lane sub-list
 constexpr int WLP = 8;       // lanes per wall particle in the wall-pressure sweep
 constexpr int AWLP = 4;      // lanes per wall particle in the adjoint's wall sweeps
 constexpr int LBLOCK = 128;  // threads per block
