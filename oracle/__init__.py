@@ -53,7 +53,7 @@ class _Params(C.Structure):
                 ("cfl", C.c_double), ("g", C.c_double * 3),
                 ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("n_phases", C.c_int32), ("reinit_every", C.c_int32),
-                ("phase", _Phase * 2), ("dim", C.c_int32)]
+                ("phase", _Phase * 2), ("dim", C.c_int32), ("periodic", C.c_int32)]
 
 
 _lib = None
@@ -110,6 +110,8 @@ def make_params(scene) -> _Params:
     P.n_phases = len(scene.phases)
     P.reinit_every = scene.reinit_every
     P.dim = getattr(scene, "dim", 3)
+    per = getattr(scene, "periodic", (0, 0, 0))
+    P.periodic = sum(1 << d for d in range(3) if per[d])
     for k, ph in enumerate(scene.phases):
         P.phase[k] = make_phase(ph)
     return P

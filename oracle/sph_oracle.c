@@ -40,7 +40,11 @@
  *     offered beside the paper's linear Eq. (EoS);
  *   - the wall pressure is evaluated after the density update of a step and
  *     before the momentum equation; the next step's continuity equation uses
- *     that same wall pressure.
+ *     that same wall pressure;
+ *   - periodic axes (not in the paper; for the momentum-conservation check of
+ *     a periodic fluid-only box): positions are wrapped into [lo, hi) after
+ *     every drift, neighbour cells wrap around, and pair vectors take the
+ *     nearest image.
  */
 #include "sph_oracle.h"
 
@@ -190,11 +194,18 @@ double orc_lattice_sigma0(double dp, double h) { return orc_lattice_sigma0_dim(d
 /* ---------------------------------------------------------------------- */
 /* neighbour search: cell-linked list with cells of side 2h (Sec. 3, item d) */
 
+static int is_periodic(const orc_sim* s, int d);
+static void nearest_image(const orc_sim* s, double r[3]);
+
 static uint32_t cell_key(const orc_sim* s, const double x[3], int32_t c[3])
 {
     int inside = 1;
     for (int d = 0; d < 3; d++) {
         c[d] = (int32_t)floor((x[d] - s->P.lo[d]) / s->cs);
+        if (is_periodic(s, d)) { /* x is wrapped; rounding may leave it one cell off */
+            if (c[d] >= s->nc[d]) c[d] -= s->nc[d];
+            if (c[d] < 0) c[d] += s->nc[d];
+        }
         if (c[d] < 0 || c[d] >= s->nc[d]) inside = 0;
     }
     if (!inside) return KEY_NONE;
@@ -248,6 +259,8 @@ static void for_neighbors(const orc_sim* s, const double* xi, const double* xs,
         for (int dy = -1; dy <= 1; dy++)
             for (int dx = -1; dx <= 1; dx++) {
                 int32_t q[3] = {c[0] + dx, c[1] + dy, c[2] + dz};
+                for (int d = 0; d < 3; d++)
+                    if (is_periodic(s, d)) q[d] = (q[d] + s->nc[d]) % s->nc[d];
                 if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= s->nc[0] ||
                     q[1] >= s->nc[1] || q[2] >= s->nc[2])
                     continue;
@@ -256,6 +269,7 @@ static void for_neighbors(const orc_sim* s, const double* xi, const double* xs,
                     int64_t j = order[k];
                     double rij[3] = {xi[0] - xs[3 * j], xi[1] - xs[3 * j + 1],
                                      xi[2] - xs[3 * j + 2]};
+                    nearest_image(s, rij);
                     double r2 = rij[0] * rij[0] + rij[1] * rij[1] + rij[2] * rij[2];
                     if (r2 >= rc2 || r2 == 0.0) continue; /* self and r = 0 skipped */
                     fn(ctx, j, rij, sqrt(r2));
@@ -266,6 +280,30 @@ static void for_neighbors(const orc_sim* s, const double* xi, const double* xs,
 static int in_grid(const orc_sim* s, int64_t i)
 {
     return s->key_f[i] != KEY_NONE;
+}
+
+static int is_periodic(const orc_sim* s, int d) { return (s->P.periodic >> d) & 1; }
+
+/* the nearest periodic image of a pair vector */
+static void nearest_image(const orc_sim* s, double r[3])
+{
+    for (int d = 0; d < 3; d++)
+        if (is_periodic(s, d)) {
+            double L = s->P.hi[d] - s->P.lo[d];
+            r[d] -= L * floor(r[d] / L + 0.5);
+        }
+}
+
+/* a position wrapped into [lo, hi) along the periodic axes */
+static void wrap_position(const orc_sim* s, double x[3])
+{
+    for (int d = 0; d < 3; d++)
+        if (is_periodic(s, d)) {
+            double L = s->P.hi[d] - s->P.lo[d];
+            double u = fmod(x[d] - s->P.lo[d], L);
+            if (u < 0.0) u += L;
+            x[d] = s->P.lo[d] + u;
+        }
 }
 
 /* dx^3, or dx^2 in 2-D: the volume of a particle (per unit depth in 2-D);
@@ -625,11 +663,13 @@ static double one_step(orc_sim* s, double dt_in)
     if (s->P.reinit_every > 0 && s->step % s->P.reinit_every == 0) reinit_density(s);
     double dt = dt_in > 0.0 ? dt_in : time_step(s);
     /* v^{n+1/2} = v^n + dt/2 a^n;  r^{n+1} = r^n + dt v^{n+1/2} */
-    for (int64_t i = 0; i < nf; i++)
+    for (int64_t i = 0; i < nf; i++) {
         for (int d = 0; d < 3; d++) {
             s->v[3 * i + d] += 0.5 * dt * s->a[3 * i + d];
             s->x[3 * i + d] += dt * s->v[3 * i + d];
         }
+        wrap_position(s, s->x + 3 * i);
+    }
     build_cells(s, nf, s->x, s->key_f, s->order_f, s->start_f);
     /* density: continuity (heavy phases) or summation (light phases) */
     double* rho_new = (double*)malloc(sizeof(double) * (size_t)(nf > 0 ? nf : 1));
@@ -699,8 +739,17 @@ orc_sim* orc_create(const orc_params* P, int64_t nf, const double* x,
     s->cs = 2.0 * P->h;
     s->n_cells = 1;
     for (int d = 0; d < 3; d++) {
-        s->nc[d] = (int32_t)ceil((P->hi[d] - P->lo[d]) / s->cs);
-        if (s->nc[d] < 1) s->nc[d] = 1;
+        double u = (P->hi[d] - P->lo[d]) / s->cs;
+        if ((P->periodic >> d) & 1) {
+            s->nc[d] = (int32_t)floor(u + 0.5);
+            if (s->nc[d] < 3 || fabs(u - s->nc[d]) > 1e-9 * (double)s->nc[d]) {
+                free(s);
+                return NULL;
+            }
+        } else {
+            s->nc[d] = (int32_t)ceil(u);
+            if (s->nc[d] < 1) s->nc[d] = 1;
+        }
         s->n_cells *= s->nc[d];
     }
     size_t f3 = sizeof(double) * 3 * (size_t)nf, f1 = sizeof(double) * (size_t)nf;
@@ -724,6 +773,7 @@ orc_sim* orc_create(const orc_params* P, int64_t nf, const double* x,
     s->start_w = (int64_t*)dup(NULL, sizeof(int64_t) * (size_t)(s->n_cells + 1));
     if (!phase)
         for (int64_t i = 0; i < nf; i++) s->phase[i] = 0;
+    for (int64_t i = 0; i < nf; i++) wrap_position(s, s->x + 3 * i);
 
     build_cells(s, nw, s->xw, s->key_w, s->order_w, s->start_w);
     build_cells(s, nf, s->x, s->key_f, s->order_f, s->start_f);
@@ -909,8 +959,9 @@ void orc_probe_pressure(const orc_sim* s, const double* pts, int64_t n,
         for (int64_t j = 0; j < s->nf; j++) {
             if (!in_grid(s, j)) continue;
             const double* xj = s->x + 3 * j;
-            double d0 = r[0] - xj[0], d1 = r[1] - xj[1], d2 = r[2] - xj[2];
-            double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            double dd[3] = {r[0] - xj[0], r[1] - xj[1], r[2] - xj[2]};
+            nearest_image(s, dd);
+            double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
             if (r2 >= rc2) continue;
             const orc_phase* ph = &s->P.phase[s->phase[j]];
             double Vj = ph->rho0 * V0 / s->rho[j];
@@ -933,8 +984,9 @@ static double liquid_fraction(const orc_sim* s, const int64_t* cand, int64_t nc,
     for (int64_t c = 0; c < nc; c++) {
         int64_t j = cand[c];
         const double* xj = s->x + 3 * j;
-        double d0 = r[0] - xj[0], d1 = r[1] - xj[1], d2 = r[2] - xj[2];
-        double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        double dd[3] = {r[0] - xj[0], r[1] - xj[1], r[2] - xj[2]};
+        nearest_image(s, dd);
+        double r2 = dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2];
         if (r2 >= rc2) continue;
         phi += s->P.phase[0].rho0 * V0 / s->rho[j] * W_of(s, sqrt(r2));
     }
@@ -961,8 +1013,9 @@ void orc_gauge_height(const orc_sim* s, const double* g, int64_t n, double dz, d
         int64_t nc = 0;
         for (int64_t j = 0; j < s->nf; j++) {
             if (!in_grid(s, j) || s->phase[j] != 0) continue;
-            double d0 = x - s->x[3 * j], d1 = y - s->x[3 * j + 1];
-            if (d0 * d0 + d1 * d1 < rc2) cand[nc++] = j;
+            double dd[3] = {x - s->x[3 * j], y - s->x[3 * j + 1], 0.0};
+            nearest_image(s, dd);
+            if (dd[0] * dd[0] + dd[1] * dd[1] < rc2) cand[nc++] = j;
         }
         int64_t K = (int64_t)floor((zhi - zlo) / dz);
         double out = zlo;

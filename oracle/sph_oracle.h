@@ -50,6 +50,8 @@ typedef struct {
     int32_t reinit_every; /* reinitialise at steps n with n % k == 0; 0 = never */
     orc_phase phase[2];
     int32_t dim;          /* 3, or 2: particles in one x-z plane (all y equal) */
+    int32_t periodic;     /* bit d set: axis d is periodic with period hi - lo, an
+                           * integer number (>= 3) of cells of side 2h */
 } orc_params;
 
 typedef struct orc_sim orc_sim;
@@ -67,7 +69,8 @@ void orc_riemann(double rhoL, double UL, double pL, double rhoR, double UR,
                  double pR, double c, int32_t limiter, double out[4]);
 double orc_lattice_sigma0(double dp, double h);
 
-/* rho may be NULL: hydrostatic density from phase z_top and g */
+/* rho may be NULL: hydrostatic density from phase z_top and g; returns NULL
+ * when a periodic axis is not a whole number (>= 3) of cells */
 orc_sim* orc_create(const orc_params* P, int64_t nf, const double* x,
                     const double* v, const double* rho, const int32_t* phase,
                     int64_t nw, const double* xw);

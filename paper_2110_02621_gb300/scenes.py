@@ -346,6 +346,29 @@ def two_phase_still_tank(n: Tuple[int, int] = (12, 6), dp: float = 0.01,
         wall_pos=wall, reinit_every=1, steps=100)
 
 
+def periodic_box(m: Tuple[int, int, int] = (1, 1, 1), dp: float = 0.01, jitter: float = 0.0,
+                 vel_scale: float = 0.0, rho_jitter: float = 0.0, seed: int = 20211006,
+                 eos: str = "linear", mu: float = 0.0) -> Scene:
+    """A fluid-only box periodic along all three axes, filled with a lattice
+    of spacing dp (optionally jittered by +-jitter dp, with random velocities
+    of scale vel_scale and density excesses of relative scale rho_jitter), no
+    walls, g = 0.  With h = 1.3 dp a period must be a whole number of 2h
+    cells and of dp: 13 m particles = 5 m cells along each axis."""
+    rng = np.random.default_rng(seed)
+    n = tuple(13 * k for k in m)
+    L = tuple(v * dp for v in n)
+    fluid = lattice(n, dp)
+    if jitter:
+        fluid = fluid + rng.uniform(-jitter, jitter, fluid.shape) * dp
+    vel = rng.normal(size=fluid.shape) * vel_scale if vel_scale else np.zeros_like(fluid)
+    rho = 1000.0 * (1.0 + rho_jitter * rng.uniform(-1.0, 1.0, len(fluid)))
+    return Scene(name=f"periodic_box_{n[0]}x{n[1]}x{n[2]}_dp{dp:g}", dp=dp, h=1.3 * dp, c0=10.0,
+                 g=(0.0, 0.0, 0.0), lo=(0.0, 0.0, 0.0), hi=L,
+                 phases=[Phase(rho0=1000.0, eos=eos, mu=mu, z_top=0.0)],
+                 fluid_pos=fluid, fluid_vel=vel, fluid_phase=np.zeros(len(fluid), np.int32),
+                 wall_pos=np.zeros((0, 3)), periodic=(1, 1, 1), reinit_every=0, rho_init=rho)
+
+
 def jittered_blob(n: Tuple[int, int, int] = (16, 16, 16), dp: float = 0.01,
                   jitter: float = 0.05, vel_scale: float = 0.1,
                   rho_jitter: float = 0.0, seed: int = SEED_JITTER,

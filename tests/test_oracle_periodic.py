@@ -1,0 +1,86 @@
+"""Pins of the oracle's periodic axes (the periodic fluid-only box in which
+the method's pair antisymmetry conserves total momentum to round-off):
+
+  - a lattice filling a periodic box has no boundary: every particle sees the
+    full-lattice number density sigma0 (computed by an independent lattice
+    sum), and at uniform density it is at rest (zero rates);
+  - a jittered, moving periodic box conserves total momentum to round-off
+    over many steps, with particles crossing the faces;
+  - translating every particle by the same vector (modulo the period) leaves
+    every rate unchanged;
+  - a particle's neighbours near a face are the brute-force nearest-image set;
+  - a period that is not a whole number (>= 3) of 2h cells is refused.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2110_02621_gb300 import scenes as S
+
+
+def test_full_periodic_lattice_has_the_lattice_number_density_everywhere():
+    sc = S.periodic_box()
+    o = oracle.OracleSim(sc, rho=np.full(sc.n_fluid, 1000.0))
+    sig = o.fluid()["sigma"]
+    s0 = oracle.lattice_sigma0(sc.dp, sc.h)
+    assert np.allclose(sig, s0, rtol=1e-12, atol=0)
+    drho, a = o.rates()
+    assert np.abs(drho).max() < 1e-9 * 1000.0
+    assert np.abs(a).max() < 1e-9
+
+
+@pytest.mark.parametrize("eos", ["linear", "tait"])
+def test_periodic_box_conserves_momentum_to_round_off(eos):
+    sc = S.periodic_box(jitter=0.3, vel_scale=0.2, rho_jitter=0.003, eos=eos, mu=1e-3)
+    o = oracle.OracleSim(sc)
+    m = 1000.0 * sc.dp ** 3
+    f0 = o.fluid()
+    P0 = m * f0["v"].sum(axis=0)
+    scale = m * np.abs(f0["v"]).sum()
+    o.step(60, 2e-4)
+    f = o.fluid()
+    P = m * f["v"].sum(axis=0)
+    assert np.abs(P - P0).max() < 1e-12 * scale
+    # particles crossed the faces and were wrapped back into [lo, hi)
+    assert np.all(f["x"] >= 0.0) and np.all(f["x"] < np.array(sc.hi))
+    moved = np.abs(f["x"] - f0["x"]) > 0.5 * np.array(sc.hi)
+    assert moved.any()
+    assert o.diagnostics()[7] == 0.0
+
+
+def test_rates_are_invariant_under_a_periodic_translation():
+    sc = S.periodic_box(jitter=0.3, vel_scale=0.2, rho_jitter=0.003)
+    o1 = oracle.OracleSim(sc)
+    d1, a1 = o1.rates()
+    shift = np.array([0.0371, -0.0519, 0.0823])
+    L = np.array(sc.hi)
+    x2 = np.mod(sc.fluid_pos + shift, L)
+    o2 = oracle.OracleSim(dataclasses.replace(sc, fluid_pos=x2))
+    d2, a2 = o2.rates()
+    assert np.abs(d2 - d1).max() < 1e-9 * np.abs(d1).max()
+    assert np.abs(a2 - a1).max() < 1e-9 * np.abs(a1).max()
+
+
+def test_neighbours_across_the_faces_are_the_nearest_images():
+    sc = S.periodic_box(jitter=0.3)
+    o = oracle.OracleSim(sc, rho=np.full(sc.n_fluid, 1000.0))
+    x = o.fluid()["x"]
+    L = np.array(sc.hi)
+    corner = int(np.argmin(np.linalg.norm(x, axis=1)))  # next to three faces
+    for i in (corner, 0, len(x) // 2):
+        f, _ = o.neighbors(i)
+        d = x - x[i]
+        d -= L * np.floor(d / L + 0.5)
+        r = np.linalg.norm(d, axis=1)
+        brute = np.where((r > 0) & (r < 2 * sc.h))[0]
+        assert np.array_equal(np.sort(f), brute)
+        assert len(brute) > 40
+
+
+def test_a_period_must_be_whole_cells():
+    sc = S.periodic_box()
+    bad = dataclasses.replace(sc, hi=(sc.hi[0] + 0.3 * sc.dp, sc.hi[1], sc.hi[2]))
+    with pytest.raises(RuntimeError):
+        oracle.OracleSim(bad)
