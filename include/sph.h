@@ -81,7 +81,8 @@ typedef struct {
     double gamma_p;     /* penalty strength gamma_p (1 in the paper)          */
     double cfl;         /* time-step coefficient (0.25, Sec. 2.6)             */
     double g[3];        /* body force [m/s^2]                                 */
-    double lo[3];       /* grid origin; particles must stay in [lo, hi)       */
+    double lo[3];       /* grid origin; particles must stay in [lo, hi)       *
+                         * (along non-periodic axes)                         */
     double hi[3];
     int32_t n_phases;   /* 1 or 2                                             */
     int32_t reinit_every; /* density reinitialisation at the start of steps   *
@@ -95,6 +96,14 @@ typedef struct {
                          * fluid and wall particle in one plane y = const    *
                          * (checked), Wendland C2 with 7/(4 pi h^2), masses  *
                          * rho0 dx^2 per unit depth                          */
+    int32_t periodic;   /* bit d (1 = x, 2 = y, 4 = z) set: axis d is         *
+                         * periodic with period hi - lo, which must be a      *
+                         * whole number >= 3 of 2h cells (to 1e-9); particles *
+                         * are wrapped into [lo, hi) at create and after each *
+                         * drift, pairs use the nearest image.  Not in the    *
+                         * paper (a periodic fluid-only box conserves total   *
+                         * momentum by pair antisymmetry).  0 = none; y may   *
+                         * not be periodic in 2-D                            */
 } sph_params;
 
 /* Fluid particles.  rho may be NULL: each particle then starts from the

@@ -48,6 +48,14 @@ sph_status validate(const sph_params* P, const sph_fluid* F, const sph_wall* W, 
             return bad(msg, "phase eos/density/reinit/penalty out of range");
     }
     double cs = 2.0 * P->h;
+    if (P->periodic & ~7) return bad(msg, "periodic is a mask of bits 1 (x), 2 (y), 4 (z)");
+    if (P->dim == 2 && (P->periodic & 2)) return bad(msg, "dim = 2: y cannot be periodic");
+    for (int d = 0; d < 3; ++d)
+        if ((P->periodic >> d) & 1) {
+            const double u = (P->hi[d] - P->lo[d]) / cs, n = std::floor(u + 0.5);
+            if (n < 3.0 || std::fabs(u - n) > 1e-9 * n)
+                return bad(msg, "a periodic axis must span a whole number (>= 3) of 2h cells");
+        }
     double cells = 1.0;
     for (int d = 0; d < 3; ++d) cells *= std::ceil((P->hi[d] - P->lo[d]) / cs);
     if (cells > (double)(sph::scan_max_len() - 2) || cells > 2.0e9)

@@ -49,6 +49,7 @@ struct Cfg {
     double g64[3];          // g in FP64 (for the body force of a moving tank)
     double ex_amp[3], ex_w; // rigid tank motion x = amp sin(w t), w = 2 pi f (Sec. 4.2)
     int32_t nx, ny, nz, n_cells;
+    int32_t periodic;       // bit d: axis d wraps (n_d cells of side cs make the period)
     int32_t n_phases;
     PhaseK<T> ph[2];
 };
@@ -117,6 +118,12 @@ __device__ __forceinline__ void rebin1(T& o, int32_t& c, T cs)
     if (o > cs) { o = sub_rn(o, cs); c += 1; }
 }
 
+// A cell index one step outside [0, n) along a periodic axis wraps around.
+__device__ __forceinline__ int32_t wrap_cell(int32_t c, int32_t n)
+{
+    return c < 0 ? c + n : (c >= n ? c - n : c);
+}
+
 template <class T>
 __device__ __forceinline__ uint32_t cell_key(const Cfg<T>& C, int32_t cx, int32_t cy, int32_t cz)
 {
@@ -171,21 +178,31 @@ __device__ __forceinline__ T eos_drho(const PhaseK<T>& P, const Cfg<T>& C, T p)
 // ------------------------------------------------------- neighbour walk
 // Visits every particle of the (up to) 27 cells around cell (cx, cy, cz) of
 // a sorted set with cell ranges start[], passing its sorted index j and the
-// shift d*cs such that r_ij = o_i - o_j - shift.
+// shift d*cs such that r_ij = o_i - o_j - shift (cells wrap along periodic
+// axes; the shift is the geometric one, so r_ij is the nearest image).
 template <class T, class Fn>
 __device__ __forceinline__ void for_cells27(const Cfg<T>& C, int32_t cx, int32_t cy, int32_t cz,
                                             const int32_t* __restrict__ start, Fn&& fn)
 {
     for (int dz = -1; dz <= 1; ++dz) {
         int z = cz + dz;
-        if (z < 0 || z >= C.nz) continue;
+        if (z < 0 || z >= C.nz) {
+            if (!(C.periodic & 4)) continue;
+            z = wrap_cell(z, C.nz);
+        }
         for (int dy = -1; dy <= 1; ++dy) {
             int y = cy + dy;
-            if (y < 0 || y >= C.ny) continue;
+            if (y < 0 || y >= C.ny) {
+                if (!(C.periodic & 2)) continue;
+                y = wrap_cell(y, C.ny);
+            }
             int row = (z * C.ny + y) * C.nx;
             for (int dx = -1; dx <= 1; ++dx) {
                 int x = cx + dx;
-                if (x < 0 || x >= C.nx) continue;
+                if (x < 0 || x >= C.nx) {
+                    if (!(C.periodic & 1)) continue;
+                    x = wrap_cell(x, C.nx);
+                }
                 int c = row + x;
                 int b = __ldg(start + c), e = __ldg(start + c + 1);
                 T sx = T(dx) * C.cs, sy = T(dy) * C.cs, sz = T(dz) * C.cs;

@@ -98,6 +98,11 @@ __device__ __forceinline__ void kick_drift(const Cfg<T>& C, T dt, V4<T>& p, V4<T
     rebin1(p.x, c.x, C.cs);
     rebin1(p.y, c.y, C.cs);
     rebin1(p.z, c.z, C.cs);
+    if (C.periodic) {  // a step moves a particle by less than one cell
+        if (C.periodic & 1) c.x = wrap_cell(c.x, C.nx);
+        if (C.periodic & 2) c.y = wrap_cell(c.y, C.ny);
+        if (C.periodic & 4) c.z = wrap_cell(c.z, C.nz);
+    }
 }
 
 // v^{n+1/2} = v^n + dt/2 a^n, r^{n+1} = r^n + dt v^{n+1/2} (Sec. 2.6), new cell

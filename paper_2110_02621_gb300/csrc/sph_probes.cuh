@@ -15,6 +15,7 @@
 #include "sph.h"
 #include "sph_device.cuh"
 #include "sph_setup.cuh"
+#include "sph_sweeps.cuh"
 
 namespace sph {
 
@@ -41,21 +42,33 @@ __device__ __forceinline__ void for_fluid_near(const Cfg<double>& D, const InitC
                                                double pz, const int32_t* __restrict__ start,
                                                const V4<T>* __restrict__ pos, int lane, int nlanes, Fn&& fn)
 {
-    const double ux = px - I.lo[0], uy = py - I.lo[1], uz = pz - I.lo[2];
+    // along a periodic axis the point is first wrapped into [0, period)
+    auto wrapped = [&](double u, int32_t n, int bit) {
+        if (!(D.periodic & bit)) return u;
+        const double L = (double)n * I.cs;
+        u = fmod(u, L);
+        return u < 0.0 ? u + L : u;
+    };
+    const double ux = wrapped(px - I.lo[0], D.nx, 1), uy = wrapped(py - I.lo[1], D.ny, 2),
+                 uz = wrapped(pz - I.lo[2], D.nz, 4);
     const int32_t cx = probe_cell(ux, I.cs, D.nx), cy = probe_cell(uy, I.cs, D.ny),
                   cz = probe_cell(uz, I.cs, D.nz);
     const double rc2 = D.rc2;
+    // z, y, xx: the geometric cells (their shift); zm, ym, xm: where they are stored
     for (int z = cz - 1; z <= cz + 1; ++z) {
-        if (z < 0 || z >= D.nz) continue;
+        int zm = z;
+        if (!row_axis(zm, D.nz, D.periodic & 4)) continue;
         const double bz = uz - (double)z * I.cs;
         for (int y = cy - 1; y <= cy + 1; ++y) {
-            if (y < 0 || y >= D.ny) continue;
+            int ym = y;
+            if (!row_axis(ym, D.ny, D.periodic & 2)) continue;
             const double by = uy - (double)y * I.cs;
-            const int row = (z * D.ny + y) * D.nx;
+            const int row = (zm * D.ny + ym) * D.nx;
             for (int xx = cx - 1; xx <= cx + 1; ++xx) {
-                if (xx < 0 || xx >= D.nx) continue;
+                int xm = xx;
+                if (!row_axis(xm, D.nx, D.periodic & 1)) continue;
                 const double bx = ux - (double)xx * I.cs;
-                const int c = row + xx;
+                const int c = row + xm;
                 const int b = __ldg(start + c), e = __ldg(start + c + 1);
                 for (int j = b + lane; j < e; j += nlanes) {
                     const V4<T> o = pos[j];

@@ -20,16 +20,24 @@ struct InitCfg {
 };
 
 // cell of an FP64 position: c = floor((x - lo)/cs) in FP64, offset x - lo - c cs
-// clamped into [0, cs] before rounding to T.
+// clamped into [0, cs] before rounding to T; along a periodic axis x - lo is
+// first wrapped into [0, period).
 template <class T>
 __device__ __forceinline__ void bin_fp64(const Cfg<T>& C, const InitCfg& I, const double* x,
                                          int4& c, V4<T>& o)
 {
     int32_t cc[3];
     T oo[3];
+    const int32_t nd[3] = {C.nx, C.ny, C.nz};
     for (int d = 0; d < 3; ++d) {
         double u = x[d] - I.lo[d];
+        if ((C.periodic >> d) & 1) {  // into [0, n cs): the period is n whole cells
+            const double L = (double)nd[d] * I.cs;
+            u = fmod(u, L);
+            if (u < 0.0) u += L;
+        }
         double f = floor(u / I.cs);
+        if (((C.periodic >> d) & 1) && f > (double)(nd[d] - 1)) f = (double)(nd[d] - 1);
         cc[d] = (f < -1e9) ? -1000000000 : (f > 1e9 ? 1000000000 : (int32_t)f);
         double r = u - f * I.cs;
         r = r < 0.0 ? 0.0 : (r > I.cs ? I.cs : r);
@@ -151,6 +159,11 @@ __global__ void k_wall_normals(Cfg<double> D, int32_t n, const int32_t* __restri
     if (c.w >= 0) {
         for_cells27(D, c.x, c.y, c.z, wstart, [&](int j, double, double, double) {
             double rx = xw - x[3 * j], ry = yw - x[3 * j + 1], rz = zw - x[3 * j + 2];
+            if (D.periodic) {  // nearest image along the periodic axes
+                if (D.periodic & 1) rx -= D.nx * D.cs * rint(rx / (D.nx * D.cs));
+                if (D.periodic & 2) ry -= D.ny * D.cs * rint(ry / (D.ny * D.cs));
+                if (D.periodic & 4) rz -= D.nz * D.cs * rint(rz / (D.nz * D.cs));
+            }
             double r2 = rx * rx + ry * ry + rz * rz;
             if (r2 >= D.rc2 || r2 == 0.0) return;
             double F = kernel_F(D, sqrt(r2));

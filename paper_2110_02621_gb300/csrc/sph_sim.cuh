@@ -128,6 +128,7 @@ Cfg<T> make_cfg(const sph_params& P, const int32_t dims[3])
     C.ny = dims[1];
     C.nz = dims[2];
     C.n_cells = dims[0] * dims[1] * dims[2];
+    C.periodic = P.periodic;
     C.n_phases = P.n_phases;
     for (int k = 0; k < 2; ++k) {
         const sph_phase& ph = P.phase[k < P.n_phases ? k : 0];
@@ -176,7 +177,9 @@ class Sim final : public SimBase {
         cs_ = 2.0 * P.h;
         n_cells_ = 1;
         for (int d = 0; d < 3; ++d) {
-            dims_[d] = (int32_t)std::ceil((P.hi[d] - P.lo[d]) / cs_);
+            const double u = (P.hi[d] - P.lo[d]) / cs_;
+            // a periodic axis is a whole number of cells (checked by the ABI)
+            dims_[d] = (P.periodic >> d) & 1 ? (int32_t)std::floor(u + 0.5) : (int32_t)std::ceil(u);
             if (dims_[d] < 1) dims_[d] = 1;
             n_cells_ *= dims_[d];
         }
@@ -430,6 +433,10 @@ class Sim final : public SimBase {
     {
         if (P_.n_phases != 1 || P_.phase[0].density != SPH_DENSITY_CONTINUITY) {
             err = "the adjoint covers one phase with continuity density";
+            return SPH_ERR_UNSUPPORTED;
+        }
+        if (P_.periodic) {
+            err = "the adjoint covers runs without periodic axes";
             return SPH_ERR_UNSUPPORTED;
         }
         if (ck_.empty()) {

@@ -104,6 +104,42 @@ __device__ __forceinline__ void group_kahan(T& s, T& c)
     }
 }
 
+// The y or z cell of a stencil row, wrapped along a periodic axis; false when
+// it lies outside a non-periodic grid.
+__device__ __forceinline__ bool row_axis(int32_t& v, int32_t n, bool periodic)
+{
+    if (v >= 0 && v < n) return true;
+    if (!periodic) return false;
+    v = wrap_cell(v, n);
+    return true;
+}
+
+// One stencil row whose x-neighbour cells wrap around a periodic x (the
+// target's cell is the first or last along x): its three cells are not one
+// contiguous range, so each is scanned in turn; lane l of NL takes the
+// candidates at positions l, l + NL, ... of the three cells' concatenation.
+template <int NL, class T, class Fn>
+__device__ __forceinline__ void scan_row_wrapped(const Cfg<T>& C, int row, int cx, const int32_t* __restrict__ start,
+                                                 const V4<T>* __restrict__ pts, int l, T xl, T x0, T xr, T ys,
+                                                 T zs, int cyz, Fn&& fn)
+{
+    const int cells[3] = {wrap_cell(cx - 1, C.nx), cx, wrap_cell(cx + 1, C.nx)};
+    const T xs[3] = {xl, x0, xr};
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int b = __ldg(start + row + cells[k]), e = __ldg(start + row + cells[k] + 1);
+#pragma unroll 1
+        for (int j = b + ((l - v) % NL + NL) % NL; j < e; j += NL) {
+            const V4<T> pj = pts[j];
+            const T rx = xs[k] - pj.x, ry = ys - pj.y, rz = zs - pj.z;
+            const T r2 = dist2(rx, ry, rz);
+            if (r2 < C.rc2 && r2 > T(0)) fn(j, rx, ry, rz, r2, cyz | k);
+        }
+        v += e - b;
+    }
+}
+
 // Lane l's share (every LP-th candidate) of the 27 cells around cell c of a
 // sorted set with cell ranges start[]: fn(j, rx, ry, rz, r2, code) for every
 // candidate with 0 < r^2 < (2h)^2, o = the target's offset, code = the
@@ -116,18 +152,24 @@ __device__ __forceinline__ void scan_share(const Cfg<T>& C, const int4& c, const
     const int xa = c.x > 0 ? c.x - 1 : 0;
     const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
     const T xl = o.x + C.cs, xr = o.x - C.cs;  // o_x - dx cs for dx = -1, +1
+    // along a periodic x the first and last cells' rows wrap (not contiguous)
+    const bool wrap_x = (C.periodic & 1) && (c.x == 0 || c.x == C.nx - 1);
     for (int dz = -1; dz <= 1; ++dz) {
-        const int z = c.z + dz;
-        if (z < 0 || z >= C.nz) continue;
+        int z = c.z + dz;
+        if (!row_axis(z, C.nz, C.periodic & 4)) continue;
         const T zs = o.z - T(dz) * C.cs;
         for (int dy = -1; dy <= 1; ++dy) {
-            const int y = c.y + dy;
-            if (y < 0 || y >= C.ny) continue;
+            int y = c.y + dy;
+            if (!row_axis(y, C.ny, C.periodic & 2)) continue;
             const T ys = o.y - T(dy) * C.cs;
             const int row = (z * C.ny + y) * C.nx;
+            const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
+            if (wrap_x) {
+                scan_row_wrapped<LP>(C, row, c.x, start, pts, l, xl, o.x, xr, ys, zs, cyz, fn);
+                continue;
+            }
             const int b = __ldg(start + row + xa), e = __ldg(start + row + xb + 1);
             const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
-            const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
 #pragma unroll 4
             for (int j = b + l; j < e; j += LP) {
                 const V4<T> pj = pts[j];
@@ -155,18 +197,24 @@ __device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const 
     const int xa = c.x > 0 ? c.x - 1 : 0;
     const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
     const T xl = o.x + C.cs, xr = o.x - C.cs;  // o_x - dx cs for dx = -1, +1
+    // along a periodic x the first and last cells' rows wrap (not contiguous)
+    const bool wrap_x = (C.periodic & 1) && (c.x == 0 || c.x == C.nx - 1);
     for (int dz = -1; dz <= 1; ++dz) {
-        const int z = c.z + dz;
-        if (z < 0 || z >= C.nz) continue;
+        int z = c.z + dz;
+        if (!row_axis(z, C.nz, C.periodic & 4)) continue;
         const T zs = o.z - T(dz) * C.cs;
         for (int dy = -1; dy <= 1; ++dy) {
-            const int y = c.y + dy;
-            if (y < 0 || y >= C.ny) continue;
+            int y = c.y + dy;
+            if (!row_axis(y, C.ny, C.periodic & 2)) continue;
             const T ys = o.y - T(dy) * C.cs;
             const int row = (z * C.ny + y) * C.nx;
+            const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
+            if (wrap_x) {
+                scan_row_wrapped<LP>(C, row, c.x, start, pts, l, xl, o.x, xr, ys, zs, cyz, fn);
+                continue;
+            }
             const int b = __ldg(start + row + xa), e = __ldg(start + row + xb + 1);
             const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
-            const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
             // the row's three cells in turn, each with its constant x shift;
             // j runs on across them, so the lanes' shares stay interleaved
             int j = b + l;
@@ -199,18 +247,24 @@ __device__ __forceinline__ void scan_compact(const Cfg<T>& C, const int4& c, con
     const int xa = c.x > 0 ? c.x - 1 : 0;
     const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
     const T xl = o.x + C.cs, xr = o.x - C.cs;
+    // along a periodic x the first and last cells' rows wrap (not contiguous)
+    const bool wrap_x = (C.periodic & 1) && (c.x == 0 || c.x == C.nx - 1);
     for (int dz = -1; dz <= 1; ++dz) {
-        const int z = c.z + dz;
-        if (z < 0 || z >= C.nz) continue;
+        int z = c.z + dz;
+        if (!row_axis(z, C.nz, C.periodic & 4)) continue;
         const T zs = o.z - T(dz) * C.cs;
         for (int dy = -1; dy <= 1; ++dy) {
-            const int y = c.y + dy;
-            if (y < 0 || y >= C.ny) continue;
+            int y = c.y + dy;
+            if (!row_axis(y, C.ny, C.periodic & 2)) continue;
             const T ys = o.y - T(dy) * C.cs;
             const int row = (z * C.ny + y) * C.nx;
+            const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
+            if (wrap_x) {
+                scan_row_wrapped<NL>(C, row, c.x, start, pts, l, xl, o.x, xr, ys, zs, cyz, fn);
+                continue;
+            }
             const int b = __ldg(start + row + xa), e = __ldg(start + row + xb + 1);
             const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
-            const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
 #pragma unroll 1
             for (int j = b + l; j < e; j += NL) {
                 const V4<T> pj = pts[j];

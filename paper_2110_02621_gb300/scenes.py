@@ -369,6 +369,39 @@ def periodic_box(m: Tuple[int, int, int] = (1, 1, 1), dp: float = 0.01, jitter: 
                  wall_pos=np.zeros((0, 3)), periodic=(1, 1, 1), reinit_every=0, rho_init=rho)
 
 
+def periodic_channel(m: Tuple[int, int] = (1, 1), nz: int = 10, dp: float = 0.01, layers: int = 3,
+                     dim: int = 3, eos: str = "tait") -> Scene:
+    """Water at rest between a floor and a roof of wall particles, periodic
+    along x (and y in 3-D): 13 m_x x 13 m_y x nz particles (13 m_x x nz in
+    the 2-D form, in the plane y = 0), g = -9.81 z, hydrostatic density; the
+    walls span the whole period."""
+    nx = 13 * m[0]
+    ny = 13 * m[1] if dim == 3 else 1
+    Lx, Ly = nx * dp, ny * dp
+    h = 1.3 * dp
+    H = nz * dp
+    if dim == 3:
+        fluid = lattice((nx, ny, nz), dp)
+        wl = lattice((nx, ny, layers), dp, origin=(0.0, 0.0, -layers * dp))
+        wu = lattice((nx, ny, layers), dp, origin=(0.0, 0.0, H))
+        lo = (0.0, 0.0, -layers * dp - 2 * h)
+        hi = (Lx, Ly, H + layers * dp + 2 * h)
+        per = (1, 1, 0)
+    else:
+        fluid = lattice2d((nx, nz), dp)
+        wl = lattice2d((nx, layers), dp, origin=(0.0, -layers * dp))
+        wu = lattice2d((nx, layers), dp, origin=(0.0, H))
+        lo = (0.0, -2 * h, -layers * dp - 2 * h)
+        hi = (Lx, 2 * h, H + layers * dp + 2 * h)
+        per = (1, 0, 0)
+    wall = np.concatenate([wl, wu])
+    return Scene(name=f"periodic_channel_{nx}x{ny}x{nz}_dp{dp:g}_{dim}d", dp=dp, h=h,
+                 c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G), lo=lo, hi=hi,
+                 phases=[Phase(rho0=1000.0, eos=eos, z_top=H)], fluid_pos=fluid,
+                 fluid_vel=np.zeros_like(fluid), fluid_phase=np.zeros(len(fluid), np.int32),
+                 wall_pos=wall, periodic=per, reinit_every=1, dim=dim)
+
+
 def jittered_blob(n: Tuple[int, int, int] = (16, 16, 16), dp: float = 0.01,
                   jitter: float = 0.05, vel_scale: float = 0.1,
                   rho_jitter: float = 0.0, seed: int = SEED_JITTER,

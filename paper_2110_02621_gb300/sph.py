@@ -50,7 +50,8 @@ class sph_params(C.Structure):
                 ("gamma_tait", C.c_double), ("gamma_p", C.c_double), ("cfl", C.c_double),
                 ("g", C.c_double * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("n_phases", C.c_int32), ("reinit_every", C.c_int32),
-                ("phase", sph_phase * 2), ("precision", C.c_int32), ("dim", C.c_int32)]
+                ("phase", sph_phase * 2), ("precision", C.c_int32), ("dim", C.c_int32),
+                ("periodic", C.c_int32)]
 
 
 class sph_fluid(C.Structure):
@@ -156,6 +157,8 @@ def make_params(scene, precision: int = SPH_FP32) -> sph_params:
                                penalty=int(bool(ph.penalty)))
     P.precision = precision
     P.dim = getattr(scene, "dim", 3)
+    per = getattr(scene, "periodic", (0, 0, 0))
+    P.periodic = sum(1 << d for d in range(3) if per[d])
     return P
 
 

@@ -84,3 +84,27 @@ def test_a_period_must_be_whole_cells():
     bad = dataclasses.replace(sc, hi=(sc.hi[0] + 0.3 * sc.dp, sc.hi[1], sc.hi[2]))
     with pytest.raises(RuntimeError):
         oracle.OracleSim(bad)
+
+
+@pytest.mark.parametrize("dim", [3, 2])
+def test_walls_of_a_periodic_channel_see_no_ends(dim):
+    """Floor and roof spanning a periodic x (and y): every wall particle's
+    normal is exactly vertical -- an edge at the period's ends would tilt the
+    normals there -- and the hydrostatic extrapolation holds at every wall
+    particle with fluid support, ends included (nearly incompressible linear
+    EOS, as in the non-periodic pin)."""
+    sc = S.periodic_channel(dim=dim, eos="linear")
+    sc = dataclasses.replace(sc, c0=1e4)
+    o = oracle.OracleSim(sc)
+    w = o.wall()
+    n = w["normal"]
+    inner = np.isclose(sc.wall_pos[:, 2], -0.5 * sc.dp) | np.isclose(sc.wall_pos[:, 2], sc.phases[0].z_top + 0.5 * sc.dp)
+    assert np.abs(n[:, 0]).max() < 1e-12 and np.abs(n[:, 1]).max() < 1e-12
+    assert np.all(np.abs(np.abs(n[inner, 2]) - 1.0) < 1e-12)
+    H = sc.phases[0].z_top
+    has = w["pw"] != 0.0
+    zw = sc.wall_pos[:, 2]
+    floor = has & (zw < 0)
+    expect = 1000.0 * 9.81 * (H - zw[floor])
+    assert floor.sum() > 10
+    assert np.max(np.abs(w["pw"][floor] - expect)) < 1e-6 * 1000 * 9.81 * H
