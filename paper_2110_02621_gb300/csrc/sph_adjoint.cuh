@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
         if (live) {
             const V4<T> nn = wnrm[w];
             const int4 c = wcell[w];
-            scan_compact<AWLP>(C, c, pw, fstart, pos, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact<false, AWLP>(C, c, pw, fstart, pos, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 // scan vector is x_w - x_f; the pair vector of the fluid is x_f - x_w
                 const V4<T> pf = pos[j], vf = vel[j], Aj = tA[j];
                 WallMomAdj<T> o;
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
         T xx = T(0), xy = T(0), xz = T(0), ux = T(0), uy = T(0), uz = T(0), pb = T(0), rb = T(0);
         T sp = T(0), spc = T(0), svv = T(0);
         T c0h = T(0), muh = T(0), muf = T(0), gpf = T(0);
-        for_neighbors(
+        for_neighbors<false>(
             C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
             [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
                 const V4<T> vj = vel[j], Aj = tA[j];
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_continuity(
         const T Di = tX[i].w;
         const T k = C.inv_c0, m2 = T(2) * P.m;
         T xx = T(0), xy = T(0), xz = T(0), ux = T(0), uy = T(0), uz = T(0), pb = T(0), rb = T(0), cb = T(0);
-        for_neighbors(
+        for_neighbors<false>(
             C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos1, wpos_prev,
             [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
                 const V4<T> vj = vel[j];
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_continuity(
         T Gp = T(0), Gr = T(0), Gc = T(0);
         if (live) {
             const int4 c = wcell[w];
-            scan_compact<AWLP>(C, c, pw, fstart, pos1, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact<false, AWLP>(C, c, pw, fstart, pos1, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 const V4<T> pf = pos1[j], vf = vel[j];
                 WallContAdj<T> o;
                 wall_continuity_adj(C, P, -rx, -ry, -rz, r2, vf.x, vf.y, vf.z, P.rho0 + drho1[j], pf.w, rho_w,

@@ -943,9 +943,15 @@ class Sim final : public SimBase {
     sph_status neighbors(const V4<T>* pts, const int4* cell)
     {
         if (nf_ == 0) return SPH_OK;
-        SPH_KERNEL(SPH_K_NEIGHBORS, 1,
-                   k_neighbors<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
-                       C_, nf_, fstart_, wstart_, pts, wpos_, cell, nbf_, nbw_, ncnt_, wtag_, d_tag_));
+        {
+            // the periodic form only where an axis wraps: the others compile its code out
+            auto launch = [&](auto kernel) {
+                kernel<<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                    C_, nf_, fstart_, wstart_, pts, wpos_, cell, nbf_, nbw_, ncnt_, wtag_, d_tag_);
+            };
+            SPH_KERNEL(SPH_K_NEIGHBORS, 1,
+                       P_.periodic ? launch(k_neighbors<T, true>) : launch(k_neighbors<T, false>));
+        }
         return SPH_OK;
     }
 
@@ -953,11 +959,15 @@ class Sim final : public SimBase {
     sph_status wall_pressure(const V4<T>* vel_cur)
     {
         if (nw_ == 0) return SPH_OK;
-        SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
-                   k_wall_pressure<T><<<grid_for((int64_t)nw_ * WLP), BLOCK, 0, stream>>>(C_, nw_, fstart_, wpos_,
-                                                                                         wcell_, pos_[0],
-                                                                           vel_cur, wrho_, wtag_, d_tag_,
-                                                                           d_geff_, d_active_));
+        {
+            // the periodic form only where an axis wraps: the others compile its code out
+            auto launch = [&](auto kernel) {
+                kernel<<<grid_for((int64_t)nw_ * WLP), BLOCK, 0, stream>>>(
+                    C_, nw_, fstart_, wpos_, wcell_, pos_[0], vel_cur, wrho_, wtag_, d_tag_, d_geff_, d_active_);
+            };
+            SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
+                       P_.periodic ? launch(k_wall_pressure<T, true>) : launch(k_wall_pressure<T, false>));
+        }
         return SPH_OK;
     }
 
@@ -966,10 +976,15 @@ class Sim final : public SimBase {
     sph_status momentum(const V4<T>* vel_cur, V4<T>* vel_out, const int4* cell, const int32_t* phase)
     {
         if (nf_ == 0) return SPH_OK;
-        SPH_KERNEL(SPH_K_MOMENTUM, 1,
-                   k_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
-                       C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_cur, cell, phase, wpos_, wrho_, wnrm_,
-                       d_dt_, d_geff_, acc_, vel_out, sigma_, d_vmax_, d_flags_));
+        {
+            // the periodic form only where an axis wraps: the others compile its code out
+            auto launch = [&](auto kernel) {
+                kernel<<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                    C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_cur, cell, phase, wpos_, wrho_, wnrm_,
+                    d_dt_, d_geff_, acc_, vel_out, sigma_, d_vmax_, d_flags_);
+            };
+            SPH_KERNEL(SPH_K_MOMENTUM, 1, P_.periodic ? launch(k_momentum<T, true>) : launch(k_momentum<T, false>));
+        }
         return SPH_OK;
     }
 
@@ -1007,10 +1022,16 @@ class Sim final : public SimBase {
                            comp_[q], cell_[q], id_[q], phase_[q]));
             sph_status sn = neighbors(pos_[1], cell_[q]);
             if (sn != SPH_OK) return sn;
-            SPH_KERNEL(SPH_K_CONTINUITY, 1,
-                       k_continuity<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
-                           C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[1], vel_[q], drho_[1], cell_[q],
-                           phase_[q], wpos_, wrho_, d_dt_, pos_[0], vel_[p], drho_[0], acc_, sigma_));
+            {
+                // the periodic form only where an axis wraps: the others compile its code out
+                auto launch = [&](auto kernel) {
+                    kernel<<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                        C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[1], vel_[q], drho_[1], cell_[q], phase_[q],
+                        wpos_, wrho_, d_dt_, pos_[0], vel_[p], drho_[0], acc_, sigma_);
+                };
+                SPH_KERNEL(SPH_K_CONTINUITY, 1,
+                           P_.periodic ? launch(k_continuity<T, true>) : launch(k_continuity<T, false>));
+            }
         }
         sph_status s = wall_pressure(vel_[p]);
         if (s != SPH_OK) return s;

@@ -20,6 +20,9 @@
 // sub-lists and combine the LP partial sums with a fixed xor-shuffle tree
 // (deterministic).  A lane whose sub-list overflowed scans its share of the
 // 27 cells directly instead.
+//
+// The kernels and scans take PER = true for runs with periodic axes, so that
+// the wrap-around code is compiled out of the others.
 #pragma once
 
 #include "sph_kernels.cuh"
@@ -144,7 +147,7 @@ __device__ __forceinline__ void scan_row_wrapped(const Cfg<T>& C, int row, int c
 // sorted set with cell ranges start[]: fn(j, rx, ry, rz, r2, code) for every
 // candidate with 0 < r^2 < (2h)^2, o = the target's offset, code = the
 // 6-bit cell shift of j.
-template <class T, class Fn>
+template <bool PER, class T, class Fn>
 __device__ __forceinline__ void scan_share(const Cfg<T>& C, const int4& c, const V4<T>& o,
                                            const int32_t* __restrict__ start, const V4<T>* __restrict__ pts,
                                            int l, Fn&& fn)
@@ -153,14 +156,14 @@ __device__ __forceinline__ void scan_share(const Cfg<T>& C, const int4& c, const
     const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
     const T xl = o.x + C.cs, xr = o.x - C.cs;  // o_x - dx cs for dx = -1, +1
     // along a periodic x the first and last cells' rows wrap (not contiguous)
-    const bool wrap_x = (C.periodic & 1) && (c.x == 0 || c.x == C.nx - 1);
+    const bool wrap_x = PER && (C.periodic & 1) && (c.x == 0 || c.x == C.nx - 1);
     for (int dz = -1; dz <= 1; ++dz) {
         int z = c.z + dz;
-        if (!row_axis(z, C.nz, C.periodic & 4)) continue;
+        if (!row_axis(z, C.nz, PER && (C.periodic & 4))) continue;
         const T zs = o.z - T(dz) * C.cs;
         for (int dy = -1; dy <= 1; ++dy) {
             int y = c.y + dy;
-            if (!row_axis(y, C.ny, C.periodic & 2)) continue;
+            if (!row_axis(y, C.ny, PER && (C.periodic & 2))) continue;
             const T ys = o.y - T(dy) * C.cs;
             const int row = (z * C.ny + y) * C.nx;
             const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
@@ -189,7 +192,7 @@ __device__ __forceinline__ void scan_share(const Cfg<T>& C, const int4& c, const
 // sorted set with cell ranges start[]: fn(j, rx, ry, rz, r2, code) for every
 // candidate with 0 < r^2 < (2h)^2, o = the target's offset, code = the
 // 6-bit cell shift of j.
-template <class T, class Fn>
+template <bool PER, class T, class Fn>
 __device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const V4<T>& o,
                                            const int32_t* __restrict__ start, const V4<T>* __restrict__ pts,
                                            int l, Fn&& fn)
@@ -198,14 +201,14 @@ __device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const 
     const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
     const T xl = o.x + C.cs, xr = o.x - C.cs;  // o_x - dx cs for dx = -1, +1
     // along a periodic x the first and last cells' rows wrap (not contiguous)
-    const bool wrap_x = (C.periodic & 1) && (c.x == 0 || c.x == C.nx - 1);
+    const bool wrap_x = PER && (C.periodic & 1) && (c.x == 0 || c.x == C.nx - 1);
     for (int dz = -1; dz <= 1; ++dz) {
         int z = c.z + dz;
-        if (!row_axis(z, C.nz, C.periodic & 4)) continue;
+        if (!row_axis(z, C.nz, PER && (C.periodic & 4))) continue;
         const T zs = o.z - T(dz) * C.cs;
         for (int dy = -1; dy <= 1; ++dy) {
             int y = c.y + dy;
-            if (!row_axis(y, C.ny, C.periodic & 2)) continue;
+            if (!row_axis(y, C.ny, PER && (C.periodic & 2))) continue;
             const T ys = o.y - T(dy) * C.cs;
             const int row = (z * C.ny + y) * C.nx;
             const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
@@ -239,7 +242,7 @@ __device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const 
 // candidate: for the rare fall-back scans of over-full sub-lists and for the
 // per-wall kernels, where code size and registers matter more than the last
 // instruction per candidate.
-template <int NL = LP, class T, class Fn>
+template <bool PER, int NL = LP, class T, class Fn>
 __device__ __forceinline__ void scan_compact(const Cfg<T>& C, const int4& c, const V4<T>& o,
                                              const int32_t* __restrict__ start, const V4<T>* __restrict__ pts,
                                              int l, Fn&& fn)
@@ -248,14 +251,14 @@ __device__ __forceinline__ void scan_compact(const Cfg<T>& C, const int4& c, con
     const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
     const T xl = o.x + C.cs, xr = o.x - C.cs;
     // along a periodic x the first and last cells' rows wrap (not contiguous)
-    const bool wrap_x = (C.periodic & 1) && (c.x == 0 || c.x == C.nx - 1);
+    const bool wrap_x = PER && (C.periodic & 1) && (c.x == 0 || c.x == C.nx - 1);
     for (int dz = -1; dz <= 1; ++dz) {
         int z = c.z + dz;
-        if (!row_axis(z, C.nz, C.periodic & 4)) continue;
+        if (!row_axis(z, C.nz, PER && (C.periodic & 4))) continue;
         const T zs = o.z - T(dz) * C.cs;
         for (int dy = -1; dy <= 1; ++dy) {
             int y = c.y + dy;
-            if (!row_axis(y, C.ny, C.periodic & 2)) continue;
+            if (!row_axis(y, C.ny, PER && (C.periodic & 2))) continue;
             const T ys = o.y - T(dy) * C.cs;
             const int row = (z * C.ny + y) * C.nx;
             const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
@@ -279,7 +282,7 @@ __device__ __forceinline__ void scan_compact(const Cfg<T>& C, const int4& c, con
 }
 
 // --------------------------------------------------------- neighbour lists
-template <class T>
+template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_neighbors(
     Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
     const V4<T>* __restrict__ pos, const V4<T>* __restrict__ wpos, const int4* __restrict__ cell,
@@ -296,13 +299,13 @@ __global__ void __launch_bounds__(LBLOCK) k_neighbors(
         const int tag = *d_tag;
         const size_t stride = (size_t)n * LP;
         size_t at = t;
-        scan_rows(C, c, o, fstart, pos, l, [&](int j, T, T, T, T, int code) {
+        scan_rows<PER>(C, c, o, fstart, pos, l, [&](int j, T, T, T, T, int code) {
             if (nf < SUBF) nbf[at] = (j << 6) | code;
             at += stride;
             ++nf;
         });
         at = t;
-        scan_rows(C, c, o, wstart, wpos, l, [&](int w, T, T, T, T, int code) {
+        scan_rows<PER>(C, c, o, wstart, wpos, l, [&](int w, T, T, T, T, int code) {
             if (nw < SUBW) nbw[at] = (w << 6) | code;
             at += stride;
             ++nw;
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(LBLOCK) k_neighbors(
 // Visits lane l's neighbours of particle i: its sub-list entries, or, for an
 // over-full sub-list, its share of the 27 cells.
 // ff(j, p_j, rx, ry, rz, r2) for fluid, fw(w, p_w, rx, ry, rz, r2) for walls.
-template <class T, class FF, class FW>
+template <bool PER, class T, class FF, class FW>
 __device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t, const V4<T>& pi, const int4& c,
                                               const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw,
                                               int32_t count, const int32_t* __restrict__ fstart,
@@ -337,7 +340,7 @@ __device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t,
             ff(j, pj, rx, ry, rz, dist2(rx, ry, rz));
         }
     } else {
-        scan_share(C, c, pi, fstart, pos, t % LP,
+        scan_share<PER>(C, c, pi, fstart, pos, t % LP,
                    [&](int j, T rx, T ry, T rz, T r2, int) { ff(j, pos[j], rx, ry, rz, r2); });
     }
     if (nw <= SUBW) {
@@ -353,7 +356,7 @@ __device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t,
             fw(w, pw, rx, ry, rz, dist2(rx, ry, rz));
         }
     } else {
-        scan_share(C, c, pi, wstart, wpos, t % LP,
+        scan_share<PER>(C, c, pi, wstart, wpos, t % LP,
                    [&](int w, T rx, T ry, T rz, T r2, int) { fw(w, wpos[w], rx, ry, rz, r2); });
     }
 }
@@ -371,7 +374,7 @@ __device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t,
 // compensated sum.  The
 // EOS then gives p^{n+1}.  Particles outside the grid keep their state and
 // get a = 0 (their momentum outputs are written here: nobody reads them).
-template <class T>
+template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_continuity(
     Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
     const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw, const int32_t* __restrict__ cnt,
@@ -405,7 +408,7 @@ __global__ void __launch_bounds__(LBLOCK) k_continuity(
     T drdt = T(0);
     if (P.density == 1) {
         T s = lead ? C.W0 : T(0), e = T(0);
-        for_neighbors(C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
+        for_neighbors<PER>(C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
                       [&](int, const V4<T>&, T, T, T, T r2) { kahan_add(s, e, kernel_W(C, r2 * p_rsqrt(r2))); },
                       [&](int, const V4<T>&, T, T, T, T r2) { kahan_add(s, e, kernel_W(C, r2 * p_rsqrt(r2))); });
         group_kahan(s, e);
@@ -413,7 +416,7 @@ __global__ void __launch_bounds__(LBLOCK) k_continuity(
     } else {
         T s = T(0);
         const T kc = C.inv_c0;
-        for_neighbors(
+        for_neighbors<PER>(
             C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
             [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
                 const V4<T> vj = vel[j];
@@ -460,7 +463,7 @@ __device__ __forceinline__ T wall_density(const PhaseK<T>& P, const Cfg<T>& C, T
 // fluid support (not tagged by this step's neighbour build) get p_w = 0 and
 // rho_w = rho0 at once; the others split the fluid of their 27 cells over WLP
 // lanes.  rho_w = rho0 + EOS^-1(p_w) per phase, at least rho0/2.
-template <class T>
+template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
     Cfg<T> C, int32_t nw, const int32_t* __restrict__ fstart, V4<T>* __restrict__ wpos,
     const int4* __restrict__ wcell, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel,
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
             const V4<T> ge = *geff;
             const int4 c = wcell[w];
             const V4<T> pw = wpos[w];
-            scan_compact<WLP>(C, c, pw, fstart, pos, t % WLP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact<PER, WLP>(C, c, pw, fstart, pos, t % WLP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 const T W = kernel_W(C, r2 * p_rsqrt(r2));
                 const T p_f = reinterpret_cast<const T*>(pos + j)[3];
                 const T rho_f = vel[j].w;
@@ -514,7 +517,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
 // the next reinitialisation (own phase and walls for continuity phases,
 // everything for summation phases; stored as sigma - sigma^0 from a
 // compensated sum) and U_max for the next dt.
-template <class T>
+template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_momentum(
     Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
     const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw, const int32_t* __restrict__ cnt,
@@ -599,7 +602,7 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
                     }
                     kahan_add(sg, se, W);
                 };
-            for_neighbors(C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos, fluid_pair, wall_pair);
+            for_neighbors<PER>(C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos, fluid_pair, wall_pair);
             const V4<T> ge = *geff;
             ax = group_sum(ax) + ge.x;
             ay = group_sum(ay) + ge.y;
