@@ -269,7 +269,7 @@ static void for_neighbors(const orc_sim* s, const double* xi, const double* xs,
                     int64_t j = order[k];
                     double rij[3] = {xi[0] - xs[3 * j], xi[1] - xs[3 * j + 1],
                                      xi[2] - xs[3 * j + 2]};
-                    nearest_image(s, rij);
+                    if (s->P.periodic) nearest_image(s, rij);
                     double r2 = rij[0] * rij[0] + rij[1] * rij[1] + rij[2] * rij[2];
                     if (r2 >= rc2 || r2 == 0.0) continue; /* self and r = 0 skipped */
                     fn(ctx, j, rij, sqrt(r2));
