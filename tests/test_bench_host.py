@@ -64,3 +64,18 @@ def test_reference_arm_prints_its_line():
     assert line["value"] > 0 and line["unit"] == "M particle-steps/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_streaming_roofline_arithmetic():
+    """Algorithmic bytes per kernel over its time, against the copy peak."""
+    import bench
+    kus = {"predict": 10.0, "scan": 4.0, "scatter": 2.0, "gather": 8.0, "momentum": 50.0}
+    r = bench.streaming_roofline(kus, 100_000, 50_000, 6800.0)
+    assert set(r) == {"predict", "scan", "scatter", "gather"}
+    assert r["predict"]["bytes"] == 100_000 * bench.BYTES_PER_PARTICLE["predict"]
+    assert r["scan"]["bytes"] == 50_000 * bench.BYTES_PER_CELL_SCAN
+    gbs = 100_000 * bench.BYTES_PER_PARTICLE["gather"] / 8e-6 / 1e9
+    assert r["gather"]["GB/s"] == round(gbs, 1)
+    assert r["gather"]["frac"] == round(gbs / 6800.0, 4)
+    assert "momentum" not in r
+    assert bench.streaming_roofline({}, 10, 10, 6800.0) == {}
