@@ -41,7 +41,7 @@ WORKLOAD = "dam_break_80k"
 
 # Algorithmic floating-point operations per in-support pair (add, sub, mul,
 # div, sqrt = 1; fma = 2), counted from the pair formulas as the kernels
-# evaluate them (kernel table).
+# evaluate them.
 FLOPS_PAIR = {
     "momentum_ff": 50,      # Riemann p*, limiter, pressure force, sigma
     "momentum_fw": 40,      # Eq. (RSatWall) pressure force, sigma (penalty rarely active)
@@ -52,7 +52,7 @@ FLOPS_PAIR = {
 }
 # Algorithmic bytes per fluid particle of the streaming kernels (unique state
 # read and written), per cell for the scan, per active wall for the wall
-# pressure (kernel table)
+# pressure
 BYTES_PER_PARTICLE = {"predict": 100, "scatter": 28, "gather": 212, "neighbors": 400, "continuity": 500,
                       "momentum": 500}
 BYTES_PER_CELL_SCAN = 8
