@@ -53,6 +53,8 @@ class Params:
     sigma0: float            # lattice number density (reading of Sec. 2.5)
     normals: torch.Tensor    # (nw, 3) wall normals, Eq. (normalVectors)
     xw: torch.Tensor         # (nw, 3) wall positions
+    lo: Optional[torch.Tensor] = None      # (3,) grid origin
+    period: Optional[torch.Tensor] = None  # (3,) period of each periodic axis, 0 elsewhere
 
 
 def params_from_scene(sc, normals: np.ndarray, sigma0: float) -> Params:
@@ -62,7 +64,34 @@ def params_from_scene(sc, normals: np.ndarray, sigma0: float) -> Params:
                   gamma_tait=sc.gamma_tait, g=torch.tensor(sc.g, dtype=F64),
                   penalty=bool(ph.penalty), reinit_every=sc.reinit_every,
                   sigma0=sigma0, normals=torch.tensor(normals, dtype=F64),
-                  xw=torch.tensor(np.asarray(sc.wall_pos, np.float64).reshape(-1, 3)))
+                  xw=torch.tensor(np.asarray(sc.wall_pos, np.float64).reshape(-1, 3)),
+                  lo=torch.tensor(sc.lo, dtype=F64),
+                  period=torch.tensor([(sc.hi[d] - sc.lo[d]) if getattr(sc, "periodic", (0, 0, 0))[d] else 0.0
+                                       for d in range(3)], dtype=F64))
+
+
+# ------------------------------------------------------------ periodic axes
+def _periodic(P) -> bool:
+    return P is not None and P.period is not None and bool((P.period > 0).any())
+
+
+def image(r, P):
+    """The nearest periodic image of pair vectors r (n, 3): a shift by whole
+    periods, constant in the positions (derivative 1)."""
+    if not _periodic(P):
+        return r
+    L = torch.where(P.period > 0, P.period, torch.ones_like(P.period))
+    k = torch.where(P.period > 0, torch.round(r.detach() / L), torch.zeros_like(r))
+    return r - k * L
+
+
+def wrap(x, P):
+    """Positions wrapped into [lo, lo + period) along the periodic axes."""
+    if not _periodic(P):
+        return x
+    L = torch.where(P.period > 0, P.period, torch.ones_like(P.period))
+    k = torch.where(P.period > 0, torch.floor((x.detach() - P.lo) / L), torch.zeros_like(x))
+    return x - k * L
 
 
 # ------------------------------------------------------------ kernel, EOS
@@ -107,14 +136,33 @@ def riemann(rhoL, UL, pL, rhoR, UR, pR, c):
 
 
 # ------------------------------------------------------------ pair lists
-def fluid_pairs(x: torch.Tensor, h: float):
-    """Directed pairs (i, j), i != j, with 0 < |x_i - x_j| < 2h."""
+def _torus(pts: np.ndarray, P):
+    """Points shifted into the box [0, size) of a k-d tree that is toroidal
+    along the periodic axes (the others get a box far larger than the
+    points' extent, so that nothing wraps there), and the box."""
+    lo, per = P.lo.numpy(), P.period.numpy()
+    if len(pts) == 0:
+        return pts, np.where(per > 0, per, 1.0)
+    base = pts.min(axis=0)
+    box = np.where(per > 0, per, 4.0 * (np.ptp(pts, axis=0) + 1.0))
+    shifted = np.where(per > 0, np.mod(pts - lo, np.where(per > 0, per, 1.0)), pts - base)
+    return np.minimum(shifted, np.nextafter(box, 0)), box
+
+
+def fluid_pairs(x: torch.Tensor, h: float, P=None):
+    """Directed pairs (i, j), i != j, with 0 < |x_i - x_j| < 2h (nearest
+    images along periodic axes)."""
     xn = x.detach().numpy()
-    pr = cKDTree(xn).query_pairs(2.0 * h, output_type="ndarray")
+    if _periodic(P):
+        sh, box = _torus(xn, P)
+        tree = cKDTree(sh, boxsize=box)
+    else:
+        tree = cKDTree(xn)
+    pr = tree.query_pairs(2.0 * h, output_type="ndarray")
     if len(pr) == 0:
         z = torch.zeros(0, dtype=torch.int64)
         return z, z
-    d = xn[pr[:, 0]] - xn[pr[:, 1]]
+    d = image(torch.from_numpy(xn[pr[:, 0]] - xn[pr[:, 1]]), P).numpy()
     r2 = (d * d).sum(axis=1)
     pr = pr[(r2 < 4.0 * h * h) & (r2 > 0.0)]
     i = np.concatenate([pr[:, 0], pr[:, 1]])
@@ -122,23 +170,28 @@ def fluid_pairs(x: torch.Tensor, h: float):
     return torch.from_numpy(i), torch.from_numpy(j)
 
 
-def wall_pairs(x: torch.Tensor, xw: torch.Tensor, h: float):
-    """Pairs (fluid i, wall w) with 0 < |x_i - x_w| < 2h."""
+def wall_pairs(x: torch.Tensor, xw: torch.Tensor, h: float, P=None):
+    """Pairs (fluid i, wall w) with 0 < |x_i - x_w| < 2h (nearest images
+    along periodic axes)."""
     if xw.shape[0] == 0 or x.shape[0] == 0:
         z = torch.zeros(0, dtype=torch.int64)
         return z, z
     xn, wn = x.detach().numpy(), xw.numpy()
-    lists = cKDTree(wn).query_ball_point(xn, 2.0 * h)
+    if _periodic(P):
+        sh, box = _torus(np.concatenate([wn, xn]), P)
+        lists = cKDTree(sh[: len(wn)], boxsize=box).query_ball_point(sh[len(wn):], 2.0 * h)
+    else:
+        lists = cKDTree(wn).query_ball_point(xn, 2.0 * h)
     i = np.repeat(np.arange(len(lists)), [len(l) for l in lists])
     w = np.concatenate([np.asarray(l, np.int64) for l in lists]) if len(i) else np.zeros(0, np.int64)
-    d = xn[i] - wn[w]
+    d = image(torch.from_numpy(xn[i] - wn[w]), P).numpy()
     r2 = (d * d).sum(axis=1)
     keep = (r2 < 4.0 * h * h) & (r2 > 0.0)
     return torch.from_numpy(i[keep]), torch.from_numpy(w[keep])
 
 
-def _geom(xa, xb, ia, ib):
-    rij = xa[ia] - xb[ib]
+def _geom(xa, xb, ia, ib, P=None):
+    rij = image(xa[ia] - xb[ib], P)
     r = torch.sqrt((rij * rij).sum(dim=1))
     return rij, r
 
@@ -164,9 +217,9 @@ def continuity(x, v, rho, p, pw, rhow, P: Params, c0, pairs):
         dot = ((v_i - vstar) * gw).sum(dim=1)
         out.index_add_(0, i, 2.0 * rho[i] * (m / rho_j) * dot)
 
-    rij, r = _geom(x, x, fi, fj)
+    rij, r = _geom(x, x, fi, fj, P)
     add(fi, rij, r, rho[fj], p[fj], v[fj])
-    rij, r = _geom(x, P.xw, wi, ww)
+    rij, r = _geom(x, P.xw, wi, ww, P)
     add(wi, rij, r, rhow[ww], pw[ww], torch.zeros_like(rij))
     return out
 
@@ -176,7 +229,7 @@ def wall_pressure(x, rho, p, P: Params, c0, wpairs, nw):
     p_w = sum_f (p_f + rho_f g.r_wf) W_wf / sum_f W_wf, r_wf = r_w - r_f;
     no support: p_w = 0.  rho_w = EOS^-1(p_w), at least rho0/2."""
     wi, ww = wpairs
-    rwf = P.xw[ww] - x[wi]
+    rwf = image(P.xw[ww] - x[wi], P)
     r = torch.sqrt((rwf * rwf).sum(dim=1))
     Wk = W(r, P.h)
     num = torch.zeros(nw, dtype=F64).index_add(0, ww, (p[wi] + rho[wi] * (rwf @ P.g)) * Wk)
@@ -199,7 +252,7 @@ def momentum(x, v, rho, p, pw, rhow, P: Params, c0, gamma_p, mu, pairs):
     eta2 = 0.01 * P.h ** 2
     a = torch.zeros_like(x)
     # fluid-fluid
-    rij, r = _geom(x, x, fi, fj)
+    rij, r = _geom(x, x, fi, fj, P)
     e = -rij / r[:, None]
     F = dWdr(r, P.h) / r
     gw = F[:, None] * rij
@@ -210,7 +263,7 @@ def momentum(x, v, rho, p, pw, rhow, P: Params, c0, gamma_p, mu, pairs):
     kv = m * (2.0 * mu) * (rij * gw).sum(dim=1) / (rho[fi] * rho[fj] * (r * r + eta2))
     a = a.index_add(0, fi, kv[:, None] * (v[fi] - v[fj]))
     # fluid-wall
-    rij, r = _geom(x, P.xw, wi, ww)
+    rij, r = _geom(x, P.xw, wi, ww, P)
     F = dWdr(r, P.h) / r
     gw = F[:, None] * rij
     rho_i, p_i, rho_w, p_w = rho[wi], p[wi], rhow[ww], pw[ww]
@@ -236,9 +289,9 @@ def number_density(x, P: Params, pairs, n):
     """sigma_i = W(0) + sum_j W_ij + sum_w W_iw (one phase: all fluid)."""
     (fi, fj), (wi, ww) = pairs
     s = torch.full((n,), float(W(torch.tensor(0.0, dtype=F64), P.h)), dtype=F64)
-    _, r = _geom(x, x, fi, fj)
+    _, r = _geom(x, x, fi, fj, P)
     s = s.index_add(0, fi, W(r, P.h))
-    _, r = _geom(x, P.xw, wi, ww)
+    _, r = _geom(x, P.xw, wi, ww, P)
     return s.index_add(0, wi, W(r, P.h))
 
 
@@ -254,7 +307,8 @@ def create(x, v, rho, P: Params, c0, gamma_p, mu) -> Dict[str, torch.Tensor]:
     """The state after sph_create: p^0 = EOS(rho^0), the wall pressure, a^0
     and sigma(r^0) of the initial positions."""
     nw = P.xw.shape[0]
-    pairs = (fluid_pairs(x, P.h), wall_pairs(x, P.xw, P.h))
+    x = wrap(x, P)
+    pairs = (fluid_pairs(x, P.h, P), wall_pairs(x, P.xw, P.h, P))
     p = eos_p(rho, P, c0)
     pw, rhow = wall_pressure(x, rho, p, P, c0, pairs[1], nw)
     a = momentum(x, v, rho, p, pw, rhow, P, c0, gamma_p, mu, pairs)
@@ -270,8 +324,8 @@ def step(S, P: Params, c0, gamma_p, mu, dt: float, do_reinit: bool):
         rho = reinit(rho, S["sigma"], P)
         p = eos_p(rho, P, c0)
     vh = S["v"] + 0.5 * dt * S["a"]
-    x = S["x"] + dt * vh
-    pairs = (fluid_pairs(x, P.h), wall_pairs(x, P.xw, P.h))
+    x = wrap(S["x"] + dt * vh, P)
+    pairs = (fluid_pairs(x, P.h, P), wall_pairs(x, P.xw, P.h, P))
     drdt = continuity(x, vh, rho, p, S["pw"], S["rhow"], P, c0, pairs)
     rho1 = rho + dt * drdt
     p1 = eos_p(rho1, P, c0)

@@ -241,7 +241,7 @@ __global__ void k_adj_prep(int32_t n, T hdt, const V4<T>* __restrict__ gv, const
 // EOS^-1(p_w') and the incoming adjoint of p_w', then divided by sum_f W_wf
 // for the extrapolation's backward.  wc = 0 for walls without support
 // (their p_w' = 0 is a constant).
-template <class T>
+template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
     Cfg<T> C, int32_t nw, const int32_t* __restrict__ fstart, const V4<T>* __restrict__ wpos,
     const V2<T>* __restrict__ wrho, const V4<T>* __restrict__ wnrm, const int4* __restrict__ wcell,
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
         if (live) {
             const V4<T> nn = wnrm[w];
             const int4 c = wcell[w];
-            scan_compact<false, AWLP>(C, c, pw, fstart, pos, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact<PER, AWLP>(C, c, pw, fstart, pos, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 // scan vector is x_w - x_f; the pair vector of the fluid is x_f - x_w
                 const V4<T> pf = pos[j], vf = vel[j], Aj = tA[j];
                 WallMomAdj<T> o;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
 // included) and the adjoint of d' into tV.  Create mode (the sweeps of
 // sph_create at r^0, no kick) writes the final adjoints of x^0 and d^0 into
 // tX and of v^0 into tV.
-template <class T>
+template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
     Cfg<T> C, int32_t n, T dt, int32_t create, const int32_t* __restrict__ fstart,
     const int32_t* __restrict__ wstart, const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw,
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
         T xx = T(0), xy = T(0), xz = T(0), ux = T(0), uy = T(0), uz = T(0), pb = T(0), rb = T(0);
         T sp = T(0), spc = T(0), svv = T(0);
         T c0h = T(0), muh = T(0), muf = T(0), gpf = T(0);
-        for_neighbors<false>(
+        for_neighbors<PER>(
             C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
             [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
                 const V4<T> vj = vel[j], Aj = tA[j];
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
 // neighbour j, the term e_ji of D_j that depends on particle i), of
 // p~ = EOS(d~), the drift, both kicks and the reinitialisation.  Writes the
 // adjoint state of the step's input in its own (old) sorted order.
-template <class T>
+template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_adj_continuity(
     Cfg<T> C, int32_t n, T dt, int32_t reinit, const int32_t* __restrict__ fstart,
     const int32_t* __restrict__ wstart, const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw,
@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_continuity(
         const T Di = tX[i].w;
         const T k = C.inv_c0, m2 = T(2) * P.m;
         T xx = T(0), xy = T(0), xz = T(0), ux = T(0), uy = T(0), uz = T(0), pb = T(0), rb = T(0), cb = T(0);
-        for_neighbors<false>(
+        for_neighbors<PER>(
             C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos1, wpos_prev,
             [&](int j, const V4<T>& pj, T rx, T ry, T rz, T r2) {
                 const V4<T> vj = vel[j];
@@ -569,7 +569,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_continuity(
 
 // Per wall: adjoint of the previous wall pressure p_w^n through the
 // continuity pairs (and rho_w^n = rho0 + EOS^-1(p_w^n)).
-template <class T>
+template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_adj_wall_continuity(
     Cfg<T> C, int32_t nw, const int32_t* __restrict__ fstart, const V4<T>* __restrict__ wpos_prev,
     const V2<T>* __restrict__ wrho_prev, const int4* __restrict__ wcell, const int32_t* __restrict__ wtag,
@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_continuity(
         T Gp = T(0), Gr = T(0), Gc = T(0);
         if (live) {
             const int4 c = wcell[w];
-            scan_compact<false, AWLP>(C, c, pw, fstart, pos1, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact<PER, AWLP>(C, c, pw, fstart, pos1, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 const V4<T> pf = pos1[j], vf = vel[j];
                 WallContAdj<T> o;
                 wall_continuity_adj(C, P, -rx, -ry, -rz, r2, vf.x, vf.y, vf.z, P.rho0 + drho1[j], pf.w, rho_w,

@@ -435,10 +435,6 @@ class Sim final : public SimBase {
             err = "the adjoint covers one phase with continuity density";
             return SPH_ERR_UNSUPPORTED;
         }
-        if (P_.periodic) {
-            err = "the adjoint covers runs without periodic axes";
-            return SPH_ERR_UNSUPPORTED;
-        }
         if (ck_.empty()) {
             if (steps_ != 0) {
                 err = "taping must start right after sph_create";
@@ -503,6 +499,13 @@ class Sim final : public SimBase {
     }
 
     sph_status backward(const sph_adjoint_seed& seed, sph_adjoint_grad& grad, int32_t where) override
+    {
+        // the periodic forms of the adjoint kernels only where an axis wraps
+        return P_.periodic ? backward_impl<true>(seed, grad, where) : backward_impl<false>(seed, grad, where);
+    }
+
+    template <bool PER>
+    sph_status backward_impl(const sph_adjoint_seed& seed, sph_adjoint_grad& grad, int32_t where)
     {
         if (ck_.empty()) {
             err = "nothing was taped";
@@ -583,7 +586,7 @@ class Sim final : public SimBase {
             }
             if (nw_ > 0)
                 SPH_KERNEL(SPH_K_ADJ_WALL, 1,
-                           k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
+                           k_adj_wall_momentum<T, PER><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
                                C_, nw_, fs, WP, WR, wnrm_, wcell_, WT, TG, P0, VP, tA_, gpw_[cur], wc_, adj_param_));
             // The wall continuity adjoint reads only tX of the momentum
             // adjoint and writes only gpw and the parameter sums, so it runs
@@ -592,20 +595,20 @@ class Sim final : public SimBase {
             const bool overlap = adj_side_ && !prof_mask_ && nf_ > 0 && nw_ > 0;
             if (nf_ > 0) {
                 SPH_KERNEL(SPH_K_ADJ_MOMENTUM, 1,
-                           k_adj_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                           k_adj_momentum<T, PER><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                                C_, nf_, dt, 0, fs, wstart_, lf, lw, lc, P0, VP, R0, CQ, WP, WR, wnrm_, wc_, tA_,
                                gx_[cur], gv_[cur], GE, tX_, tV_, adj_param_));
                 if (overlap) {
                     SPH_CUDA(cudaEventRecord(adj_ev_[0], stream));
                     SPH_CUDA(cudaStreamWaitEvent(adj_side_, adj_ev_[0], 0));
-                    k_adj_wall_continuity<T><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, adj_side_>>>(
+                    k_adj_wall_continuity<T, PER><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, adj_side_>>>(
                         C_, nw_, fs, c.wpos, c.wrho, wcell_, WT, TG, P1, VP, R1, tX_, gpw_[nxt], adj_param_);
                     SPH_LAUNCH();
                     launches_[SPH_K_ADJ_WALL] += 1;
                     SPH_CUDA(cudaEventRecord(adj_ev_[1], adj_side_));
                 }
                 SPH_KERNEL(SPH_K_ADJ_CONTINUITY, 1,
-                           k_adj_continuity<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                           k_adj_continuity<T, PER><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                                C_, nf_, dt, c.reinit ? 1 : 0, fs, wstart_, lf, lw, lc, P1, VP, R1, CQ, c.wpos,
                                c.wrho, tX_, tV_, gx_[cur], IQ, adj_inv_, c.drho, c.sigma, gx_[nxt], gv_[nxt],
                                ga_[nxt], adj_param_));
@@ -613,7 +616,7 @@ class Sim final : public SimBase {
             }
             if (nw_ > 0 && !overlap)
                 SPH_KERNEL(SPH_K_ADJ_WALL, 1,
-                           k_adj_wall_continuity<T><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
+                           k_adj_wall_continuity<T, PER><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
                                C_, nw_, fs, c.wpos, c.wrho, wcell_, WT, TG, P1, VP, R1, tX_, gpw_[nxt], adj_param_));
             cur = nxt;
         }
@@ -628,12 +631,12 @@ class Sim final : public SimBase {
                        k_adj_prep<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, T(0), gv_[cur], ga_[cur], tA_));
         if (nw_ > 0)
             SPH_KERNEL(SPH_K_ADJ_WALL, 1,
-                       k_adj_wall_momentum<T><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
+                       k_adj_wall_momentum<T, PER><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
                            C_, nw_, fstart_, wpos_, wrho_, wnrm_, wcell_, wtag_, d_tag_, pos_[0], vel_[p0], tA_,
                            gpw_[cur], wc_, adj_param_));
         if (nf_ > 0) {
             SPH_KERNEL(SPH_K_ADJ_MOMENTUM, 1,
-                       k_adj_momentum<T><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
+                       k_adj_momentum<T, PER><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                            C_, nf_, T(0), 1, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_[p0], drho_[0],
                            cell_[p0], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], d_geff_, tX_, tV_,
                            adj_param_));
