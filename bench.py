@@ -478,6 +478,10 @@ def run_gpu(args):
         line["accuracy"] = accuracy(sc)
         line["adjoint"] = adjoint_block(stream)
         line["other_workloads"] = other_workloads(stream, flush)
+        try:  # reported, not fatal: the main line stands on its own
+            line["sensors"] = sensors_block(stream)
+        except Exception as e:
+            line["sensors"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc, active_mean, args.cpu_seconds)
     if rank == 0:
@@ -666,6 +670,45 @@ def other_workloads(stream, flush, steps: int = 50):
                              kus, sc.n_fluid, n_cells, float(measured_peaks().get("hbm_gbs", 6800.0)))}
         except Exception as e:  # reported, not fatal: the main line stands on its own
             out[name] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
+def sensors_block(stream, steps: int = 200):
+    """Cost of sampling the obstacle dam break's 5 pressure sensors and 4 wave
+    gauges after every step (device buffers, enqueued between asynchronous
+    steps), against the step alone: CUDA events on the library's stream."""
+    import torch
+    from paper_2110_02621_gb300 import scenes, sph
+    sc = scenes.standard("dam_break_obstacle_123k")
+    sim = sph.Simulation(sc, precision=sph.SPH_FP32, stream=stream.cuda_stream)
+    dev = torch.device("cuda")
+    pts = torch.from_numpy(sc.sensors).to(dev)
+    lines = torch.from_numpy(sc.gauges).to(dev)
+    p = torch.zeros((steps, len(pts)), dtype=torch.float64, device=dev)
+    w = torch.zeros_like(p)
+    H = torch.zeros((steps, len(lines)), dtype=torch.float64, device=dev)
+    L = sph.lib()
+    sim.step(20)
+    out = {}
+    for label, sample in (("step", False), ("step_and_sensors", True)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for k in range(steps):
+            sim.step_async(1)
+            if sample:
+                L.sph_probe_pressure(sim.ctx, pts.data_ptr(), len(pts), p[k].data_ptr(), w[k].data_ptr(),
+                                     sph.SPH_DEVICE)
+                L.sph_gauge_height(sim.ctx, lines.data_ptr(), len(lines), 0.25 * sc.dp, H[k].data_ptr(),
+                                   sph.SPH_DEVICE)
+        e1.record(stream)
+        sim.sync()
+        out[label + "_ms"] = e0.elapsed_time(e1) / steps
+    sim.close()
+    out["sensors_us_per_sample"] = 1e3 * (out["step_and_sensors_ms"] - out["step_ms"])
+    out.update({"workload": "dam_break_obstacle_123k", "n_fluid": sc.n_fluid, "n_wall": sc.n_wall,
+                "sensors": len(pts), "gauges": len(lines), "steps": steps,
+                "H_last": [round(float(v), 4) for v in H[-1].cpu()]})
     return out
 
 

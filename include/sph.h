@@ -243,7 +243,8 @@ sph_status sph_time(sph_ctx* ctx, double* t);
  *   p_k = sum_j p_j V_j W(|r_k - r_j|) / w_k   (p_k = 0 where w_k = 0),
  * j over every fluid particle of every phase inside the grid with
  * |r_k - r_j| < 2h (r = r_j included), W the Wendland C2 kernel of the run's
- * dimension; evaluated in FP64 from the current state, between steps.  w_k is
+ * dimension; evaluated from the current state between steps, pair terms in
+ * the run's precision, sums in FP64.  w_k is
  * the fluid's volume fraction at r_k (about 1 inside the fluid, 1/2 on a flat
  * free surface or a wall face).  Points may lie anywhere, outside the grid
  * included.  p and w (n doubles each; either may be NULL) receive the results.
@@ -256,7 +257,7 @@ sph_status sph_time(sph_ctx* ctx, double* t);
 sph_status sph_probe_pressure(sph_ctx* ctx, const double* pts, int32_t n,
                               double* p, double* w, int32_t where);
 
-enum { SPH_GAUGE_MAX_SAMPLES = 65536 };
+enum { SPH_GAUGE_MAX_SAMPLES = 65536, SPH_GAUGE_MAX_LINES = 65535 };
 
 /* Wave-height gauges (the gauges H_i of Sec. 4.3).  For each vertical line
  * gauges[4k..4k+3] = (x, y, z_lo, z_hi) (z along -g; in 2-D y is the plane's
@@ -268,11 +269,13 @@ enum { SPH_GAUGE_MAX_SAMPLES = 65536 };
  * sample reaches 1/2 (a dry line) and z_K when the top one does.  1/2 is the
  * value of phi on the face of a half-space of particles, so H reads the free
  * surface of the first phase (the liquid of a two-phase run); isolated drops
- * (phi below 1/2) are not counted.  Evaluated in FP64 between steps.  H
+ * (phi below 1/2) are not counted.  Evaluated between steps.  H
  * receives n doubles.  where as for sph_probe_pressure; with SPH_DEVICE a
  * line that is not finite, has z_hi < z_lo or K >= SPH_GAUGE_MAX_SAMPLES
- * yields NaN.  Errors: SPH_ERR_ARG (n < 0, NULL arrays with n > 0, dz not
- * finite and > 0, such a line in host memory), SPH_ERR_CUDA, SPH_ERR_STATE. */
+ * yields NaN.  Pair terms are evaluated in the run's precision and summed
+ * in FP64 (sph_probe_pressure alike).  Errors: SPH_ERR_ARG (n < 0 or above
+ * SPH_GAUGE_MAX_LINES, NULL arrays with n > 0, dz not finite and > 0, such a
+ * line in host memory), SPH_ERR_CUDA, SPH_ERR_STATE. */
 sph_status sph_gauge_height(sph_ctx* ctx, const double* gauges, int32_t n,
                             double dz, double* H, int32_t where);
 

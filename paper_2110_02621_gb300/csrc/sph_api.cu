@@ -263,10 +263,10 @@ sph_status sph_gauge_height(sph_ctx* ctx, const double* gauges, int32_t n, doubl
 {
     sph_status s = usable(ctx);
     if (s != SPH_OK) return s;
-    if (n < 0 || (n > 0 && (!gauges || !H)) || !(dz > 0.0) || !std::isfinite(dz) ||
+    if (n < 0 || n > SPH_GAUGE_MAX_LINES || (n > 0 && (!gauges || !H)) || !(dz > 0.0) || !std::isfinite(dz) ||
         (where != SPH_HOST && where != SPH_DEVICE)) {
-        ctx->sim->err = "n must be >= 0, gauges and H non-NULL when n > 0, dz finite and > 0; where must be "
-                        "SPH_HOST or SPH_DEVICE";
+        ctx->sim->err = "n must be in [0, SPH_GAUGE_MAX_LINES], gauges and H non-NULL when n > 0, dz finite and "
+                        "> 0; where must be SPH_HOST or SPH_DEVICE";
         return SPH_ERR_ARG;
     }
     if (where == SPH_HOST)

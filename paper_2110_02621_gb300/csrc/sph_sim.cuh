@@ -805,7 +805,7 @@ class Sim final : public SimBase {
         const int64_t threads = (int64_t)n * 32;
         SPH_KERNEL(SPH_K_OTHER, 1,
                    k_probe_pressure<T><<<(unsigned)((threads + BLOCK - 1) / BLOCK), BLOCK, 0, stream>>>(
-                       D_, I_, n, dpts, fstart_, pos_[0], drho_[0], phase_[par_], dp, dw));
+                       C_, D_, I_, n, dpts, fstart_, pos_[0], drho_[0], phase_[par_], dp, dw));
         if (host) {
             if (p) SPH_CUDA(cudaMemcpyAsync(p, dp, b1, cudaMemcpyDeviceToHost, stream));
             if (w) SPH_CUDA(cudaMemcpyAsync(w, dw, b1, cudaMemcpyDeviceToHost, stream));
@@ -822,21 +822,27 @@ class Sim final : public SimBase {
         const bool host = where == SPH_HOST;
         const size_t b1 = sizeof(double) * (size_t)n;
         const double* dg = g;
-        double *dH = H, *scratch = nullptr;
+        double* dH = H;
+        char* scratch = nullptr;  // [the lines, H (host path)], the best sample per line
+        const size_t lines_b = host ? 5 * b1 : 0;
+        SPH_CUDA(cudaMallocAsync(&scratch, lines_b + sizeof(int32_t) * (size_t)n, stream));
         if (host) {
-            SPH_CUDA(cudaMallocAsync(&scratch, 5 * b1, stream));
             SPH_CUDA(cudaMemcpyAsync(scratch, g, 4 * b1, cudaMemcpyHostToDevice, stream));
-            dg = scratch;
-            dH = scratch + 4 * (size_t)n;
+            dg = (const double*)scratch;
+            dH = (double*)scratch + 4 * (size_t)n;
         }
+        int32_t* best = (int32_t*)(scratch + lines_b);
+        SPH_CUDA(cudaMemsetAsync(best, 0xff, sizeof(int32_t) * (size_t)n, stream));  // -1: no wet sample yet
         SPH_KERNEL(SPH_K_OTHER, 1,
-                   k_gauge_height<T><<<(unsigned)n, GAUGE_BLOCK, 0, stream>>>(D_, I_, n, dg, dz, fstart_, pos_[0],
-                                                                             drho_[0], phase_[par_], dH));
-        if (host) {
-            SPH_CUDA(cudaMemcpyAsync(H, dH, b1, cudaMemcpyDeviceToHost, stream));
-            SPH_CUDA(cudaFreeAsync(scratch, stream));
-            SPH_CUDA(cudaStreamSynchronize(stream));
-        }
+                   k_gauge_crossing<T><<<dim3(GAUGE_BLOCKS_PER_LINE, (unsigned)n), GAUGE_BLOCK, 0, stream>>>(
+                       C_, D_, I_, n, dg, dz, fstart_, pos_[0], drho_[0], phase_[par_], best));
+        const int64_t threads = (int64_t)n * 32;
+        SPH_KERNEL(SPH_K_OTHER, 1,
+                   k_gauge_finish<T><<<(unsigned)((threads + BLOCK - 1) / BLOCK), BLOCK, 0, stream>>>(
+                       C_, D_, I_, n, dg, dz, fstart_, pos_[0], drho_[0], phase_[par_], best, dH));
+        if (host) SPH_CUDA(cudaMemcpyAsync(H, dH, b1, cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaFreeAsync(scratch, stream));
+        if (host) SPH_CUDA(cudaStreamSynchronize(stream));
         return SPH_OK;
     }
 

@@ -31,6 +31,7 @@ EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_sync", "sph_diagnostics_async", "sph_set_excitation", "sph_time",
            "sph_probe_pressure", "sph_gauge_height", "sph_tape_budget")
 SPH_GAUGE_MAX_SAMPLES = 65536
+SPH_GAUGE_MAX_LINES = 65535
 SPH_ERR_CAPACITY = 8
 SPH_BIN_SORT_NOALLOC_SCRATCH = 32 << 20
 KERNEL_KINDS = ("begin_step", "predict", "scan", "scatter", "gather", "neighbors",
