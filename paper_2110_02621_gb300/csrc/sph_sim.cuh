@@ -230,8 +230,15 @@ class Sim final : public SimBase {
                                                                   wid_, xw_sorted);
             k_wall_normals<T><<<grid_for(nw_), BLOCK, 0, stream>>>(D_, nw_, wstart_, wcell_, xw_sorted, wnrm_);
             SPH_LAUNCH();
+            if (P_.periodic)
+                k_wall_rows<true, T><<<grid_for(n_cells_), BLOCK, 0, stream>>>(C_, n_cells_, wstart_, wrows_);
+            else
+                k_wall_rows<false, T><<<grid_for(n_cells_), BLOCK, 0, stream>>>(C_, n_cells_, wstart_, wrows_);
+            SPH_LAUNCH();
             SPH_CUDA(cudaFreeAsync(xw_in, stream));
             SPH_CUDA(cudaFreeAsync(xw_sorted, stream));
+        } else {
+            SPH_CUDA(cudaMemsetAsync(wrows_, 0, sizeof(uint16_t) * (size_t)n_cells_, stream));
         }
 
         // ---- fluid: upload, initial density, first sort
@@ -927,6 +934,7 @@ class Sim final : public SimBase {
         if ((s = alloc(counts_, nc + 1)) != SPH_OK) return s;
         if ((s = alloc(fstart_, nc + 2)) != SPH_OK) return s;
         if ((s = alloc(wstart_, nc + 2)) != SPH_OK) return s;
+        if ((s = alloc(wrows_, nc)) != SPH_OK) return s;
         if ((s = alloc(sums_, (size_t)scan_blocks(n_cells_ + 1))) != SPH_OK) return s;
         if ((s = alloc(wpos_, nw)) != SPH_OK) return s;
         if ((s = alloc(wpos_tmp_, nw)) != SPH_OK) return s;
@@ -956,7 +964,7 @@ class Sim final : public SimBase {
             // the periodic form only where an axis wraps: the others compile its code out
             auto launch = [&](auto kernel) {
                 kernel<<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
-                    C_, nf_, fstart_, wstart_, pts, wpos_, cell, nbf_, nbw_, ncnt_, wtag_, d_tag_);
+                    C_, nf_, fstart_, wstart_, wrows_, pts, wpos_, cell, nbf_, nbw_, ncnt_, wtag_, d_tag_);
             };
             SPH_KERNEL(SPH_K_NEIGHBORS, 1,
                        P_.periodic ? launch(k_neighbors<T, true>) : launch(k_neighbors<T, false>));
@@ -1382,6 +1390,7 @@ class Sim final : public SimBase {
     int4* newcell_ = nullptr;
     int32_t *rank_ = nullptr, *tmp_src_ = nullptr, *tmp_id_ = nullptr;
     int32_t *counts_ = nullptr, *fstart_ = nullptr, *wstart_ = nullptr, *sums_ = nullptr;
+    uint16_t* wrows_ = nullptr;  // per cell: the stencil rows that hold wall particles
     V4<T>* wpos_ = nullptr;
     V4<T>* wpos_tmp_ = nullptr;
     V2<T>* wrho_ = nullptr;

@@ -192,10 +192,11 @@ __device__ __forceinline__ void scan_share(const Cfg<T>& C, const int4& c, const
 // sorted set with cell ranges start[]: fn(j, rx, ry, rz, r2, code) for every
 // candidate with 0 < r^2 < (2h)^2, o = the target's offset, code = the
 // 6-bit cell shift of j.
+// Only the rows whose bit (dz + 1) 3 + (dy + 1) is set in rows are walked.
 template <bool PER, class T, class Fn>
 __device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const V4<T>& o,
                                            const int32_t* __restrict__ start, const V4<T>* __restrict__ pts,
-                                           int l, Fn&& fn)
+                                           int l, Fn&& fn, unsigned rows = 0x1ffu)
 {
     const int xa = c.x > 0 ? c.x - 1 : 0;
     const int xb = c.x + 1 < C.nx ? c.x + 1 : C.nx - 1;
@@ -207,6 +208,7 @@ __device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const 
         if (!row_axis(z, C.nz, PER && (C.periodic & 4))) continue;
         const T zs = o.z - T(dz) * C.cs;
         for (int dy = -1; dy <= 1; ++dy) {
+            if (!((rows >> ((dz + 1) * 3 + dy + 1)) & 1u)) continue;
             int y = c.y + dy;
             if (!row_axis(y, C.ny, PER && (C.periodic & 2))) continue;
             const T ys = o.y - T(dy) * C.cs;
@@ -281,13 +283,52 @@ __device__ __forceinline__ void scan_compact(const Cfg<T>& C, const int4& c, con
     }
 }
 
+// Which of the 9 stencil rows around each cell hold wall particles: bit
+// (dz + 1) 3 + (dy + 1) of rows[k] is set when the cells of that row that
+// scan_rows walks (clamped to the grid, or wrapped along periodic axes) hold
+// any.  The walls are fixed, so this runs once, after they are binned; the
+// neighbour build then skips the empty wall rows, which are all nine for a
+// cell inside the fluid.
+template <bool PER, class T>
+__global__ void k_wall_rows(Cfg<T> C, int32_t n_cells, const int32_t* __restrict__ wstart,
+                            uint16_t* __restrict__ rows)
+{
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_cells) return;
+    const int32_t cx = k % C.nx, cy = (k / C.nx) % C.ny, cz = k / C.nx / C.ny;
+    const int xa = cx > 0 ? cx - 1 : 0;
+    const int xb = cx + 1 < C.nx ? cx + 1 : C.nx - 1;
+    const bool wrap_x = PER && (C.periodic & 1) && (cx == 0 || cx == C.nx - 1);
+    unsigned m = 0;
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+        if (!row_axis(z, C.nz, PER && (C.periodic & 4))) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            if (!row_axis(y, C.ny, PER && (C.periodic & 2))) continue;
+            const int row = (z * C.ny + y) * C.nx;
+            bool any = false;
+            if (wrap_x) {
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int x = wrap_cell(cx + dx, C.nx);
+                    any |= wstart[row + x + 1] > wstart[row + x];
+                }
+            } else {
+                any = wstart[row + xb + 1] > wstart[row + xa];
+            }
+            if (any) m |= 1u << ((dz + 1) * 3 + dy + 1);
+        }
+    }
+    rows[k] = (uint16_t)m;
+}
+
 // --------------------------------------------------------- neighbour lists
 template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_neighbors(
     Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
-    const V4<T>* __restrict__ pos, const V4<T>* __restrict__ wpos, const int4* __restrict__ cell,
-    int32_t* __restrict__ nbf, int32_t* __restrict__ nbw, int32_t* __restrict__ cnt, int32_t* __restrict__ wtag,
-    const int32_t* __restrict__ d_tag)
+    const uint16_t* __restrict__ wrows, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ wpos,
+    const int4* __restrict__ cell, int32_t* __restrict__ nbf, int32_t* __restrict__ nbw,
+    int32_t* __restrict__ cnt, int32_t* __restrict__ wtag, const int32_t* __restrict__ d_tag)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / LP, l = t % LP;
@@ -305,12 +346,17 @@ __global__ void __launch_bounds__(LBLOCK) k_neighbors(
             ++nf;
         });
         at = t;
-        scan_rows<PER>(C, c, o, wstart, wpos, l, [&](int w, T, T, T, T, int code) {
-            if (nw < SUBW) nbw[at] = (w << 6) | code;
-            at += stride;
-            ++nw;
-            wtag[w] = tag;
-        });
+        const unsigned wr = __ldg(wrows + c.w);
+        if (wr)
+            scan_rows<PER>(
+                C, c, o, wstart, wpos, l,
+                [&](int w, T, T, T, T, int code) {
+                    if (nw < SUBW) nbw[at] = (w << 6) | code;
+                    at += stride;
+                    ++nw;
+                    wtag[w] = tag;
+                },
+                wr);
     }
     cnt[t] = nf | (nw << 16);
 }
@@ -500,8 +546,10 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
             wrho[w] = V2<T>{r0, r1};
         }
     }
-    const int cnt = __syncthreads_count(has);
-    if (threadIdx.x == 0 && cnt) atomicAdd(active, (unsigned long long)cnt);
+    // walls with support, counted per warp (no block barrier: a warp whose
+    // walls had no support leaves at once)
+    const unsigned bal = __ballot_sync(0xffffffffu, has);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(active, (unsigned long long)__popc(bal));
 }
 
 // --------------------------------------------------------------- momentum
