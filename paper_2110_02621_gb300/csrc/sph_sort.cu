@@ -2,8 +2,10 @@
 // including sorting"): exclusive scan of the per-cell counts, first
 // placement by arrival rank, then the in-cell rank by particle id makes the
 // final order (key, id) independent of atomic arrival order.  The scan is one
-// block for short inputs, else a three-kernel reduce / scan-of-sums /
-// down-sweep; neither has inter-block waits.  It can clear its input behind
+// block for short inputs, else a reduce / down-sweep pair of kernels in which
+// each down-sweep block adds up the sums of the blocks before it, and for
+// long inputs (more than SCAN_DIRECT blocks) a reduce / scan-of-sums /
+// down-sweep; none has inter-block waits.  It can clear its input behind
 // itself, so the step's cell counters are zero for the next step.
 #include <cstdint>
 #include <cstdio>
@@ -13,9 +15,11 @@
 
 namespace sph {
 
-constexpr int SCAN_THREADS = 512;
-constexpr int SCAN_ITEMS = 8;
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 4096 values per block
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;  // 1024 values per block
+constexpr int SCAN_DIRECT = 512;  // block counts up to which each down-sweep block sums its predecessors
+constexpr int64_t SCAN_MAX = (int64_t)1 << 24;  // longest input
 
 __device__ __forceinline__ int32_t block_exclusive_scan(int32_t v, int32_t* total)
 {
@@ -55,25 +59,32 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int32_t* __r
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-// one block: exclusive scan of the block sums (at most SCAN_TILE of them)
+// one block: exclusive scan of the nb block sums, SCAN_TILE of them at a
+// time with a running carry
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_sums(int32_t* sums, int32_t nb)
 {
-    int base = threadIdx.x * SCAN_ITEMS;
-    int32_t v[SCAN_ITEMS], s = 0;
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        v[k] = base + k < nb ? sums[base + k] : 0;
-        s += v[k];
-    }
-    int32_t total;
-    int32_t off = block_exclusive_scan(s, &total);
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        if (base + k < nb) sums[base + k] = off;
-        off += v[k];
+    int32_t carry = 0;
+    for (int c0 = 0; c0 < nb; c0 += SCAN_TILE) {
+        const int base = c0 + threadIdx.x * SCAN_ITEMS;
+        int32_t v[SCAN_ITEMS], s = 0;
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            v[k] = base + k < nb ? sums[base + k] : 0;
+            s += v[k];
+        }
+        int32_t total;
+        int32_t off = block_exclusive_scan(s, &total) + carry;
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            if (base + k < nb) sums[base + k] = off;
+            off += v[k];
+        }
+        carry += total;
     }
 }
 
+// scanned: sums[] holds the blocks' exclusive offsets (k_scan_sums ran);
+// else it holds their totals and each block adds up those before it.
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int32_t* in, int32_t n,
-                                                            const int32_t* __restrict__ sums,
+                                                            const int32_t* __restrict__ sums, int32_t scanned,
                                                             int32_t* __restrict__ out, int32_t* clear)
 {
     int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
@@ -85,8 +96,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const int32_t* in, i
     if (clear)
         for (int k = 0; k < SCAN_ITEMS; ++k)
             if (base + k < n) clear[base + k] = 0;
+    int32_t offset;
+    if (scanned) {
+        offset = sums[blockIdx.x];
+    } else {
+        // integer sums: the order of the additions does not matter
+        int32_t before = 0;
+        for (int k = threadIdx.x; k < (int)blockIdx.x; k += SCAN_THREADS) before += sums[k];
+        block_exclusive_scan(before, &offset);
+    }
     int32_t total;
-    int32_t off = block_exclusive_scan(s, &total) + sums[blockIdx.x];
+    int32_t off = block_exclusive_scan(s, &total) + offset;
     for (int k = 0; k < SCAN_ITEMS; ++k) {
         if (base + k < n) out[base + k] = off;
         off += v[k];
@@ -119,7 +139,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(const int32_t* in,
 }
 
 int32_t scan_blocks(int64_t n) { return (int32_t)((n + SCAN_TILE - 1) / SCAN_TILE); }
-int64_t scan_max_len() { return (int64_t)SCAN_TILE * SCAN_TILE; }
+int64_t scan_max_len() { return SCAN_MAX; }
 
 int scan_exclusive(const int32_t* in, int32_t n, int32_t* out, int32_t* sums, cudaStream_t st, int32_t* clear)
 {
@@ -129,9 +149,10 @@ int scan_exclusive(const int32_t* in, int32_t n, int32_t* out, int32_t* sums, cu
     }
     int nb = scan_blocks(n);
     k_scan_reduce<<<nb, SCAN_THREADS, 0, st>>>(in, n, sums);
-    k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(sums, nb);
-    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(in, n, sums, out, clear);
-    return 3;
+    const bool direct = nb <= SCAN_DIRECT;
+    if (!direct) k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(sums, nb);
+    k_scan_down<<<nb, SCAN_THREADS, 0, st>>>(in, n, sums, direct ? 0 : 1, out, clear);
+    return direct ? 2 : 3;
 }
 
 // ------------------------------------------------- stand-alone binning API

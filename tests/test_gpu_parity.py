@@ -101,14 +101,22 @@ def check_state(g, o, ow, dp, tol_rate=TOL_RATE, tol_x=TOL_X, what="", gnorm=9.8
 
 
 # ------------------------------------------------------------ neighbour data
-@pytest.mark.parametrize("case", ["random", "on_boundaries", "ragged_empty"])
+@pytest.mark.parametrize("case", ["random", "on_boundaries", "ragged_empty", "scan_of_59k_cells",
+                                  "scan_of_1.28M_cells"])
 def test_bin_sort_bit_exact(case):
+    """(key, id) order and cell ranges bit-exact against the oracle; the
+    grids span the scan's one-block form (up to 16 k cells), its two-kernel
+    form (up to 524 k cells) and its three-kernel form."""
     import torch
     rng = np.random.default_rng(7)
     h = 0.013
     cs = 2 * h
     if case == "random":
         x = rng.uniform(0, 1, (20011, 3)) * [0.5, 0.3, 0.2]
+    elif case.startswith("scan_of"):
+        h, box = (0.005, [0.5, 0.4, 0.25]) if case == "scan_of_59k_cells" else (0.0025, [1.0, 0.5, 0.3])
+        cs = 2 * h
+        x = rng.uniform(0, 1, (200003, 3)) * box
     elif case == "on_boundaries":
         k = rng.integers(0, 9, (5003, 3)).astype(np.float64)
         x = k * cs + np.where(rng.uniform(size=(5003, 3)) < 0.5, 0.0, rng.uniform(0, cs, (5003, 3)))
