@@ -252,6 +252,33 @@ def test_still_water_8k_fp32_100_steps():
     assert d[7] == 0
 
 
+@pytest.mark.parametrize("precision", [sph.SPH_FP32, sph.SPH_FP64_PLAIN])
+def test_dam_break_80k_100_steps(precision):
+    """The benchmark's dam break (80,400 fluid, 120,234 wall particles,
+    reinitialisation every 20 steps) for 100 CFL steps in the library's own
+    launch configuration: trajectories within 1e-3 dp (FP32) or 1e-7 dp (plain
+    FP64) of the oracle, densities within 1e-5 (1e-9), the same dt at every
+    call, mass exactly conserved and no particle lost."""
+    sc = S.dam_break()
+    ref = oracle.OracleSim(sc)
+    fp32 = precision == sph.SPH_FP32
+    with sph.Simulation(sc, precision=precision) as sim:
+        m0 = sim.diagnostics()[0]
+        for _ in range(4):
+            dt = sim.step(25)
+            dref = ref.step(25)
+            assert abs(dt - dref) <= (1e-6 if fp32 else 1e-12) * dref
+        g = sim.state()
+        d = sim.diagnostics()
+    o = ref.fluid()
+    assert np.abs(g["x"] - o["x"]).max() <= (TOL_X if fp32 else 1e-7) * sc.dp
+    assert rel_inf(g["rho"], o["rho"]) <= (1e-5 if fp32 else 1e-9)
+    assert np.abs(g["v"] - o["v"]).max() <= (1e-3 if fp32 else 1e-7) * np.abs(o["v"]).max()
+    assert d[0] == m0 and d[7] == 0
+    # the column has started to collapse (t = 0.019 s)
+    assert np.abs(o["v"]).max() > 0.1
+
+
 def test_still_water_8k_fp64_plain_100_steps():
     """The still-water tank in the plain FP64 form agrees with the oracle to
     FP64 round-off."""
