@@ -298,8 +298,13 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
 // included) and the adjoint of d' into tV.  Create mode (the sweeps of
 // sph_create at r^0, no kick) writes the final adjoints of x^0 and d^0 into
 // tX and of v^0 into tV.
+// FP32: seven blocks per SM (at most 72 registers; the compiler's free choice
+// is 96, five blocks): a small spill costs less than the latency the extra
+// warps hide (185 against 209 us per step at 189 k fluid particles, one
+// GB300).  The FP64 form keeps the 166 registers it takes unbounded (capped,
+// it would spill kilobytes).
 template <class T, bool PER>
-__global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
+__global__ void __launch_bounds__(LBLOCK, sizeof(T) == 4 ? 7 : 3) k_adj_momentum(
     Cfg<T> C, int32_t n, T dt, int32_t create, const int32_t* __restrict__ fstart,
     const int32_t* __restrict__ wstart, const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw,
     const int32_t* __restrict__ cnt, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel,
@@ -447,8 +452,10 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_momentum(
 // neighbour j, the term e_ji of D_j that depends on particle i), of
 // p~ = EOS(d~), the drift, both kicks and the reinitialisation.  Writes the
 // adjoint state of the step's input in its own (old) sorted order.
+// FP32: eight blocks per SM (at most 64 registers, against 72 unbounded): 125
+// against 134 us per step at 189 k fluid particles.  FP64: its unbounded 128.
 template <class T, bool PER>
-__global__ void __launch_bounds__(LBLOCK) k_adj_continuity(
+__global__ void __launch_bounds__(LBLOCK, sizeof(T) == 4 ? 8 : 4) k_adj_continuity(
     Cfg<T> C, int32_t n, T dt, int32_t reinit, const int32_t* __restrict__ fstart,
     const int32_t* __restrict__ wstart, const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw,
     const int32_t* __restrict__ cnt, const V4<T>* __restrict__ pos1, const V4<T>* __restrict__ vel,
