@@ -290,7 +290,7 @@ sph_status sph_counters(sph_ctx* ctx, int64_t* steps, int64_t* active_wall_steps
 enum {
     SPH_K_BEGIN_STEP = 0,   /* time step from U_max, clear cell counters      */
     SPH_K_PREDICT = 1,      /* half kick, drift, new cell, cell counts        */
-    SPH_K_SCAN = 2,         /* exclusive scan of cell counts (3 launches)     */
+    SPH_K_SCAN = 2,         /* exclusive scan of cell counts (1-3 launches)   */
     SPH_K_SCATTER = 3,      /* first placement by arrival rank                */
     SPH_K_GATHER = 4,       /* (key, id) order, reinitialisation, EOS         */
     SPH_K_NEIGHBORS = 5,    /* per-particle neighbour lists (r < 2h)          */
@@ -416,7 +416,7 @@ sph_status sph_bin_sort(const double* pos, int64_t n, const double lo[3],
  * SPH_BIN_SORT_NOALLOC_SCRATCH bytes inside the library, which every GPU that
  * loads the library keeps until the process exits; the call itself allocates
  * and frees nothing.  The scratch needs 32 bytes per particle, 8 bytes per
- * grid cell and 4 bytes per 4096 cells, each of its 8 parts rounded up to 256
+ * grid cell and 4 bytes per 1024 cells, each of its 8 parts rounded up to 256
  * bytes (about 1 M particles with 0.2 M cells, or 0.5 M particles with 2 M
  * cells); larger inputs are refused with SPH_ERR_CAPACITY before any work is
  * queued.
