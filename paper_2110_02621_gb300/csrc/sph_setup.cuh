@@ -252,54 +252,105 @@ static __global__ void k_export_cells(int32_t n, const int4* __restrict__ cell,
 }
 
 // ------------------------------------------------------------- diagnostics
-// FP64 block partials of {mass, momentum x/y/z, E_kin, E_pot, U_max, escaped};
-// a single block then sums them in a fixed order (deterministic).
-template <class T>
-__global__ void k_diag_partial(Cfg<T> C, InitCfg I, int32_t n, const V4<T>* __restrict__ pos,
-                               const V4<T>* __restrict__ vel, const int4* __restrict__ cell,
-                               const int32_t* __restrict__ phase, double* __restrict__ partial)
+// FP64 sums of {mass, momentum x/y/z, E_kin, E_pot, -, escaped} and the
+// maximum of |v|^2 (field 6; its square root is taken at the end, which gives
+// the same bits as the maximum of the roots), in a fixed order
+// (deterministic): each thread accumulates a fixed grid-stride share of the
+// particles, warps and blocks reduce with fixed trees, one block combines the
+// block partials.
+constexpr int DIAG_MAX_BLOCKS = 1216;  // 8 blocks of 128 threads on each of the 152 SMs
+
+// The warp totals of the 8 fields of q (field 6 included as a sum; callers
+// reduce it separately with max): a transposing butterfly in which, at each
+// of the first three xor levels, a lane keeps half of its values and adds the
+// partner's copy of that half, so that 9 additions and 9 shuffles replace 40.
+// Lanes 4f..4f+3 end up holding the total of field f = (lane >> 2) & 7.
+__device__ __forceinline__ double warp_sum8(const double (&q)[8], int lane)
 {
-    __shared__ double sh[8][BLOCK / 32];
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (k < n) {
-        V4<T> p = pos[k], v = vel[k];
-        int4 c = cell[k];
-        // the phase picked by value: an indexed kernel parameter would go
-        // through local memory
-        double m = (double)(phase[k] == 0 ? C.ph[0].m : C.ph[1].m);
-        double vx = v.x, vy = v.y, vz = v.z;
-        double x = I.lo[0] + (double)c.x * I.cs + (double)p.x;
-        double y = I.lo[1] + (double)c.y * I.cs + (double)p.y;
-        double z = I.lo[2] + (double)c.z * I.cs + (double)p.z;
-        q[0] = m;
-        q[1] = m * vx;
-        q[2] = m * vy;
-        q[3] = m * vz;
-        q[4] = 0.5 * m * (vx * vx + vy * vy + vz * vz);
-        q[5] = -m * ((double)C.gx * x + (double)C.gy * y + (double)C.gz * z);
-        q[6] = c.w >= 0 ? sqrt(vx * vx + vy * vy + vz * vz) : 0.0;
-        q[7] = c.w >= 0 ? 0.0 : 1.0;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    double r[4], s[2];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {  // r[j] is field j + 4 b4
+        const double send = b4 ? q[j] : q[j + 4];
+        r[j] = (b4 ? q[j + 4] : q[j]) + __shfl_xor_sync(0xffffffffu, send, 16);
     }
-    // fixed trees (deterministic): xor shuffles in each warp, then the warps
-    for (int o = 16; o > 0; o >>= 1)
-        for (int f = 0; f < 8; ++f) {
-            const double y = __shfl_xor_sync(0xffffffffu, q[f], o);
-            q[f] = f == 6 ? fmax(q[f], y) : q[f] + y;
-        }
-    if ((threadIdx.x & 31) == 0)
-        for (int f = 0; f < 8; ++f) sh[f][threadIdx.x >> 5] = q[f];
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        const int f = threadIdx.x;
-        double a = sh[f][0];
-        for (int w = 1; w < BLOCK / 32; ++w) a = f == 6 ? fmax(a, sh[f][w]) : a + sh[f][w];
-        partial[blockIdx.x * 8 + f] = a;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {  // s[j] is field j + 2 b3 + 4 b4
+        const double send = b3 ? r[j] : r[j + 2];
+        s[j] = (b3 ? r[j + 2] : r[j]) + __shfl_xor_sync(0xffffffffu, send, 8);
     }
+    double u = (b2 ? s[1] : s[0]) + __shfl_xor_sync(0xffffffffu, b2 ? s[0] : s[1], 4);
+    u += __shfl_xor_sync(0xffffffffu, u, 2);
+    u += __shfl_xor_sync(0xffffffffu, u, 1);
+    return u;
 }
 
-// The 8 sums over the blocks' partials: DIAG_THREADS threads stride over the
-// blocks for each quantity, then a fixed tree combines them (deterministic).
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block stage shared by both kernels: the warps' 8 results, then thread f < 8
+// combines field f over the warps in order.
+template <int THREADS>
+__device__ __forceinline__ double block_reduce8(const double (&q)[8], double vmax2, double (&sh)[8][THREADS / 32])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const double u = warp_sum8(q, lane);
+    const double m = warp_max(vmax2);
+    const int f = (lane >> 2) & 7;
+    if ((lane & 3) == 0 && f != 6) sh[f][warp] = u;
+    if (lane == 0) sh[6][warp] = m;
+    __syncthreads();
+    double a = 0.0;
+    if (threadIdx.x < 8) {
+        const int g = threadIdx.x;
+        a = sh[g][0];
+        for (int w = 1; w < THREADS / 32; ++w) a = g == 6 ? fmax(a, sh[g][w]) : a + sh[g][w];
+    }
+    return a;
+}
+
+template <class T>
+__global__ void __launch_bounds__(BLOCK) k_diag_partial(Cfg<T> C, InitCfg I, int32_t n,
+                                                        const V4<T>* __restrict__ pos,
+                                                        const V4<T>* __restrict__ vel,
+                                                        const int4* __restrict__ cell,
+                                                        const int32_t* __restrict__ phase,
+                                                        double* __restrict__ partial)
+{
+    __shared__ double sh[8][BLOCK / 32];
+    double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double vmax2 = 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const V4<T> p = pos[k], v = vel[k];
+        const int4 c = cell[k];
+        // the phase picked by value: an indexed kernel parameter would go
+        // through local memory
+        const double m = (double)(phase[k] == 0 ? C.ph[0].m : C.ph[1].m);
+        const double vx = v.x, vy = v.y, vz = v.z;
+        const double x = I.lo[0] + (double)c.x * I.cs + (double)p.x;
+        const double y = I.lo[1] + (double)c.y * I.cs + (double)p.y;
+        const double z = I.lo[2] + (double)c.z * I.cs + (double)p.z;
+        const double v2 = vx * vx + vy * vy + vz * vz;
+        q[0] += m;
+        q[1] += m * vx;
+        q[2] += m * vy;
+        q[3] += m * vz;
+        q[4] += 0.5 * m * v2;
+        q[5] += -m * ((double)C.gx * x + (double)C.gy * y + (double)C.gz * z);
+        if (c.w >= 0)
+            vmax2 = fmax(vmax2, v2);
+        else
+            q[7] += 1.0;
+    }
+    const double a = block_reduce8<BLOCK>(q, vmax2, sh);
+    if (threadIdx.x < 8) partial[blockIdx.x * 8 + threadIdx.x] = a;
+}
+
+// The 8 results over the blocks' partials: DIAG_THREADS threads stride over
+// the blocks for each quantity, then the fixed trees combine them.
 constexpr int DIAG_THREADS = 256;
 
 static __global__ void __launch_bounds__(DIAG_THREADS) k_diag_final(int32_t nblocks,
@@ -308,25 +359,14 @@ static __global__ void __launch_bounds__(DIAG_THREADS) k_diag_final(int32_t nblo
 {
     __shared__ double sh[8][DIAG_THREADS / 32];
     double q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < nblocks; b += DIAG_THREADS)
-        for (int f = 0; f < 8; ++f) {
-            const double v = partial[b * 8 + f];
-            q[f] = f == 6 ? fmax(q[f], v) : q[f] + v;
-        }
-    for (int o = 16; o > 0; o >>= 1)
-        for (int f = 0; f < 8; ++f) {
-            const double y = __shfl_xor_sync(0xffffffffu, q[f], o);
-            q[f] = f == 6 ? fmax(q[f], y) : q[f] + y;
-        }
-    if ((threadIdx.x & 31) == 0)
-        for (int f = 0; f < 8; ++f) sh[f][threadIdx.x >> 5] = q[f];
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        const int f = threadIdx.x;
-        double a = sh[f][0];
-        for (int w = 1; w < DIAG_THREADS / 32; ++w) a = f == 6 ? fmax(a, sh[f][w]) : a + sh[f][w];
-        out[f] = a;
+    double vmax2 = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += DIAG_THREADS) {
+        for (int f = 0; f < 8; ++f)
+            if (f != 6) q[f] += partial[b * 8 + f];
+        vmax2 = fmax(vmax2, partial[b * 8 + 6]);
     }
+    const double a = block_reduce8<DIAG_THREADS>(q, vmax2, sh);
+    if (threadIdx.x < 8) out[threadIdx.x] = threadIdx.x == 6 ? sqrt(a) : a;
 }
 
 }  // namespace sph

@@ -784,6 +784,7 @@ class Sim final : public SimBase {
     sph_status diagnostics_async(double* out, int32_t where) override
     {
         int nb = grid_for(nf_ > 0 ? nf_ : 1);
+        if (nb > DIAG_MAX_BLOCKS) nb = DIAG_MAX_BLOCKS;
         SPH_KERNEL(SPH_K_OTHER, 1,
                    k_diag_partial<T><<<nb, BLOCK, 0, stream>>>(C_, I_, nf_, pos_[0], vel_[par_], cell_[par_],
                                                                phase_[par_], diag_partial_));
