@@ -26,17 +26,28 @@ DENSITY = {"continuity": 0, "summation": 1}
 REINIT = {"none": 0, "free_surface": 1, "internal": 2}
 
 
+def compile_command(src: str, out: str) -> list:
+    """The gcc command that builds the oracle library from src."""
+    return ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC",
+            "-shared", "-o", out, src, "-lm"]
+
+
+# A prebuilt library to load instead (the mutation tests load deliberately
+# broken copies of the oracle this way, in subprocesses of their own).
+_LIB_OVERRIDE = "SPH_ORACLE_LIB"
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into a shared library (gcc, FP64, no contraction)."""
+    if os.environ.get(_LIB_OVERRIDE):
+        return os.environ[_LIB_OVERRIDE]
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
                                              os.path.getmtime(_SRC[:-1] + "h"))):
         return _LIB
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     tmp = _LIB + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC",
-           "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.check_call(cmd)
+    subprocess.check_call(compile_command(_SRC, tmp))
     os.replace(tmp, _LIB)
     return _LIB
 

@@ -1,0 +1,173 @@
+"""Mutation check of the oracle's pins: each case plants one plausible
+mistake in a copy of the oracle's C source (a dropped term, a wrong sign,
+factor or exponent, transposed operands, a wrong index order), builds that
+copy on the CPU, and runs the oracle's pin files against it in a subprocess
+(``SPH_ORACLE_LIB`` makes ``oracle.lib()`` load the copy).  Every mistake
+must make at least one pin fail.  The product code is not involved; the
+mistakes exist only in temporary copies.
+
+A case whose original text no longer occurs exactly once in the oracle
+fails, so the list follows the source."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "sph_oracle.c")
+PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_2d.py", "tests/test_oracle_periodic.py",
+             "tests/test_oracle_probes.py"]
+
+# (what the mistake is, original text, mistaken text)
+MUTANTS = [
+    ('kernel normalisation',
+     '21.0 / (16.0 * PI * h * h * h)',
+     '21.0 / (15.0 * PI * h * h * h)'),
+    ('kernel power dropped',
+     'return wendland_alpha(h, dim) * t * t * t * t * (2.0 * q + 1.0);',
+     'return wendland_alpha(h, dim) * t * t * t * (2.0 * q + 1.0);'),
+    ('dW/dr sign',
+     'return -5.0 * wendland_alpha',
+     'return 5.0 * wendland_alpha'),
+    ('Tait exponent',
+     '(pow(rho / ph->rho0, gamma_tait) - 1.0)',
+     '(pow(rho / ph->rho0, gamma_tait - 1.0) - 1.0)'),
+    ('Riemann U* sign',
+     'double Ustar = U_bar + 0.5 * (pL - pR) / (c * rho_bar);',
+     'double Ustar = U_bar + 0.5 * (pR - pL) / (c * rho_bar);'),
+    ('limiter factor',
+     'fmin(3.0 * fmax(UL - UR, 0.0), c)',
+     'fmin(2.0 * fmax(UL - UR, 0.0), c)'),
+    ('P_bar operands',
+     'double P_bar = (rhoL * pR + rhoR * pL) / (rhoL + rhoR);',
+     'double P_bar = (rhoL * pL + rhoR * pR) / (rhoL + rhoR);'),
+    ('wall hydrostatic term dropped',
+     'c->num += (s->p[f] + s->rho[f] * gr) * w;',
+     'c->num += s->p[f] * w;'),
+    ('wall hydrostatic sign',
+     'c->num += (s->p[f] + s->rho[f] * gr) * w;',
+     'c->num += (s->p[f] - s->rho[f] * gr) * w;'),
+    ('multi-phase wall weight',
+     'double w = (s->P.n_phases > 1) ? W / s->rho[f] : W;',
+     'double w = W;'),
+    ('continuity factor 2',
+     'c->sum += 2.0 * rho_i * (m_j / rho_j) * dot;',
+     'c->sum += rho_i * (m_j / rho_j) * dot;'),
+    ('continuity mixture transposed',
+     'double vmix = (rho_i * v_i[d] + rho_j * v_j[d]) / (rho_i + rho_j);',
+     'double vmix = (rho_j * v_i[d] + rho_i * v_j[d]) / (rho_i + rho_j);'),
+    ('momentum rho_j -> rho_i',
+     '-2.0 * m_j * pstar / (s->rho[i] * s->rho[j]) * gw[d]',
+     '-2.0 * m_j * pstar / (s->rho[i] * s->rho[i]) * gw[d]'),
+    ('wall p* operands',
+     'double pstar = (rho_i * p_w + rho_w * p_i) / (rho_i + rho_w);',
+     'double pstar = (rho_i * p_i + rho_w * p_w) / (rho_i + rho_w);'),
+    ('penalty lambda power',
+     '(1.0 - delta) * (1.0 - delta) / dx',
+     '(1.0 - delta) / dx'),
+    ('penalty delta factor',
+     'double delta = 2.0 * r / dx * fabs(en);',
+     'double delta = r / dx * fabs(en);'),
+    ('viscosity eta',
+     '(r * r + 0.01 * s->P.h * s->P.h)',
+     '(r * r + 0.1 * s->P.h * s->P.h)'),
+    ('viscosity sign',
+     'c->a[d] += k * (c->vel[3 * i + d] - v_j[d]);',
+     'c->a[d] -= k * (c->vel[3 * i + d] - v_j[d]);'),
+    ('reinit free-surface factor',
+     'fmax(0.0, rho_star - rho_num) * ph->rho0 / rho_star',
+     'fmax(0.0, rho_star - rho_num)'),
+    ('first kick full',
+     '            s->v[3 * i + d] += 0.5 * dt * s->a[3 * i + d];\n            s->x[3 * i + d] += dt * s->v[3 * i + d];',
+     '            s->v[3 * i + d] += dt * s->a[3 * i + d];\n            s->x[3 * i + d] += dt * s->v[3 * i + d];'),
+    ('body-force dt limit',
+     'dt = fmin(dt, s->P.cfl * sqrt(s->P.h / gn));',
+     'dt = fmin(dt, s->P.cfl * sqrt(2.0 * s->P.h / gn));'),
+    ('nearest image',
+     'r[d] -= L * floor(r[d] / L + 0.5);',
+     'r[d] -= L * floor(r[d] / L);'),
+    ('cutoff shrunk',
+     'if (r2 >= rc2 || r2 == 0.0) continue;',
+     'if (r2 >= 0.95 * rc2 || r2 == 0.0) continue;'),
+    ('wall normal sign',
+     'c->psi[d] -= V * g[d];',
+     'c->psi[d] += V * g[d];'),
+    ('cell key axes',
+     'return (uint32_t)(((int64_t)c[2] * s->nc[1] + c[1]) * s->nc[0] + c[0]);',
+     'return (uint32_t)(((int64_t)c[0] * s->nc[1] + c[1]) * s->nc[2] + c[2]);'),
+    ('summation self term',
+     'sum_ctx c = {s, W_of(s, 0.0)};',
+     'sum_ctx c = {s, 0.0};'),
+    ('sensor volume',
+     'double Vj = ph->rho0 * V0 / s->rho[j];',
+     'double Vj = V0;'),
+    ('sensor normalisation',
+     'if (p_out) p_out[k] = sw > 0.0 ? spw / sw : 0.0;',
+     'if (p_out) p_out[k] = spw;'),
+    ('excitation sign',
+     's->geff[d] = s->P.g[d] + s->ex_amp[d] * w * w * sw;',
+     's->geff[d] = s->P.g[d] - s->ex_amp[d] * w * w * sw;'),
+    ('periodic wrap',
+     'if (u < 0.0) u += L;',
+     'if (u < 0.0) u += 0.5 * L;'),
+    ('hydrostatic init',
+     'double p = P->phase[k].rho0 * gz * (P->phase[k].z_top - z);',
+     'double p = P->phase[k].rho0 * gz * (z - P->phase[k].z_top);'),
+    ('stacked phases',
+     'p += P->phase[m].rho0 * gz * (P->phase[m].z_top - P->phase[m - 1].z_top);',
+     'p += P->phase[k].rho0 * gz * (P->phase[m].z_top - P->phase[m - 1].z_top);'),
+    ('E_kin factor',
+     'ek += 0.5 * m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);',
+     'ek += m * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);'),
+    ('E_pot sign',
+     'ep -= m * (s->P.g[0] * x[0] + s->P.g[1] * x[1] + s->P.g[2] * x[2]);',
+     'ep += m * (s->P.g[0] * x[0] + s->P.g[1] * x[1] + s->P.g[2] * x[2]);'),
+    ('gauge interpolation',
+     'out = i == K ? r[2] : r[2] + dz * (phi - 0.5) / (phi - phi_above);',
+     'out = r[2];'),
+    ('wall density floor',
+     's->rhow[2 * w + k] = pw < p_half ? 0.5 * ph->rho0',
+     's->rhow[2 * w + k] = pw < p_half ? 0.4 * ph->rho0'),
+    ('CFL speed term',
+     'double dt = s->P.cfl * s->P.h / (s->P.c0 + max_speed(s));',
+     'double dt = s->P.cfl * s->P.h / s->P.c0;'),
+    ('reinit number density',
+     'double rho_num = ph->rho0 * s->sigma[i] / s->sigma0;',
+     'double rho_num = ph->rho0 * s->sigma[i] / (s->sigma0 * 1.001);'),
+    ('second kick dropped',
+     '        for (int d = 0; d < 3; d++) s->v[3 * i + d] += 0.5 * dt * s->a[3 * i + d];\n    s->step++;',
+     '        for (int d = 0; d < 3; d++) s->v[3 * i + d] += 0.0 * dt * s->a[3 * i + d];\n    s->step++;'),
+    ('Ustar diffusion factor',
+     'double Ustar = U_bar + 0.5 * (pL - pR) / (c * rho_bar);',
+     'double Ustar = U_bar + (pL - pR) / (c * rho_bar);'),
+    ('penalty side',
+     'double Ppen = s->P.gamma_p * lambda * fabs(p_i * en);',
+     'double Ppen = s->P.gamma_p * lambda * p_i * en;'),
+]
+
+
+@pytest.fixture(scope="module")
+def workdir(tmp_path_factory):
+    d = tmp_path_factory.mktemp("oracle_mutants")
+    with open(os.path.join(ROOT, "oracle", "sph_oracle.h")) as fh, open(d / "sph_oracle.h", "w") as out:
+        out.write(fh.read())
+    return d
+
+
+@pytest.mark.parametrize("name,original,mistaken", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_a_planted_mistake_fails_a_pin(workdir, name, original, mistaken):
+    with open(SRC) as fh:
+        src = fh.read()
+    assert src.count(original) == 1, f"the text of case {name!r} no longer occurs once in the oracle"
+    tag = "".join(ch if ch.isalnum() else "_" for ch in name)
+    c_file = workdir / f"{tag}.c"
+    so_file = workdir / f"{tag}.so"
+    c_file.write_text(src.replace(original, mistaken))
+    subprocess.check_call(oracle.compile_command(str(c_file), str(so_file)))
+    run = subprocess.run([sys.executable, "-m", "pytest", *PIN_FILES, "-x", "-q", "-p", "no:cacheprovider"],
+                         cwd=ROOT, env=dict(os.environ, SPH_ORACLE_LIB=str(so_file)),
+                         capture_output=True, text=True, timeout=600)
+    assert run.returncode == 1, f"no pin caught: {name}\n{run.stdout[-2000:]}"

@@ -79,6 +79,27 @@ def test_neighbours_across_the_faces_are_the_nearest_images():
         assert len(brute) > 40
 
 
+def test_a_lone_particle_wraps_around_the_period():
+    """A single particle in a periodic box (g = 0, nothing to interact with)
+    moves in a straight line: after each step its position is (x0 + v t)
+    reduced modulo the period into [lo, hi), across the lower and upper
+    faces alike."""
+    box = S.periodic_box()
+    L = np.array(box.hi) - np.array(box.lo)
+    x0 = np.array([[0.2 * L[0], 0.7 * L[1], 0.5 * L[2]]])
+    v = np.array([-1.3, 0.9, 0.05]) * L[0]  # m/s: more than one period per second
+    sc = dataclasses.replace(box, fluid_pos=x0, fluid_vel=v[None, :], fluid_phase=np.zeros(1, np.int32),
+                             rho_init=None, g=(0.0, 0.0, 0.0))
+    o = oracle.OracleSim(sc, rho=np.array([1000.0]))
+    dt, t = 1e-2, 0.0
+    for _ in range(8):
+        o.step(10, dt)
+        t += 10 * dt
+        expect = np.array(box.lo) + np.mod(x0[0] + v * t - np.array(box.lo), L)
+        assert np.allclose(o.fluid()["x"][0], expect, rtol=0, atol=1e-12)
+    assert t * abs(v[0]) > L[0]  # crossed the lower x face at least once
+
+
 def test_a_period_must_be_whole_cells():
     sc = S.periodic_box()
     bad = dataclasses.replace(sc, hi=(sc.hi[0] + 0.3 * sc.dp, sc.hi[1], sc.hi[2]))

@@ -246,6 +246,57 @@ def torn_fluid_under_a_roof(eos="tait"):
     return sc, np.array([300.0])
 
 
+
+def test_wall_pressure_of_two_phases_leaves_out_the_heavy_phase():
+    """Sec. 2.3: in multi-phase flow the extrapolation weights are divided by
+    the fluid density so that the heavy phase's contribution vanishes.  A wall
+    particle midway between a water particle (p = 100 Pa) and an air particle
+    (p = 0), g = 0: the water's share of p_w is rho_air / (rho_air +
+    rho_water), about 1e-3, where plain kernel weights would give 1/2 (as they
+    do, exactly, for two water particles)."""
+    phases = [S.Phase(eos="linear", rho0=1000.0, reinit="none"),
+              S.Phase(eos="linear", rho0=1.0, reinit="none")]
+    d = 0.008
+    sc = _pair_scene([-2 * d, 0.0, 0.0], [0.0] * 3, [0.0] * 3, phases, 1, walls=[[-d, 0.0, 0.0]])
+    rho = np.array([1001.0, 1.0])  # p_water = c0^2 (1001 - 1000) = 100 Pa, p_air = 0
+    pw = oracle.OracleSim(sc, rho=rho).wall()["pw"][0]
+    assert 0.0 < pw < 2e-3 * 100.0
+    assert pw == pytest.approx(100.0 * 1.0 / (1.0 + 1001.0), rel=1e-12)
+    one = _pair_scene([-2 * d, 0.0, 0.0], [0.0] * 3, [0.0] * 3, phases[:1], 0, walls=[[-d, 0.0, 0.0]])
+    pw1 = oracle.OracleSim(one, rho=np.array([1001.0, 1000.0])).wall()["pw"][0]
+    assert pw1 == pytest.approx(50.0, rel=1e-12)
+
+
+def test_wall_star_pressure_is_the_acoustic_impedance_average():
+    """The fluid-wall pair of Eq. (RSatWall) at rest is the linearised
+    (acoustic) Riemann problem between the fluid state (rho_i, p_i) and the
+    wall state (rho_w, p_w) with one sound speed: p* = (Z_w p_i + Z_i p_w) /
+    (Z_i + Z_w), Z = rho c, each side's pressure weighted by the other side's
+    impedance.  One particle 0.9 dx above one wall particle with gravity, so
+    that p_w = p_i + rho_i g dz differs from p_i, and a soft linear EOS
+    (c0 = 1 m/s) so that rho_w differs from rho_i; p* is read back from the
+    particle's acceleration a_z = -2 m_w p* / (rho_i rho_w) dW/dr + g_z."""
+    dp, h = 0.01, 0.013
+    z = 0.9 * dp
+    phases = [S.Phase(eos="linear", rho0=1000.0, reinit="none")]
+    sc = S.Scene(name="wallpair", dp=dp, h=h, c0=1.0, g=(0.0, 0.0, -9.81), lo=(-0.05, -0.05, -0.05),
+                 hi=(0.05, 0.05, 0.05), phases=phases, fluid_pos=np.array([[0.0, 0.0, z]]),
+                 fluid_vel=np.zeros((1, 3)), fluid_phase=np.zeros(1, np.int32),
+                 wall_pos=np.array([[0.0, 0.0, 0.0]]), reinit_every=0)
+    rho_i = 1050.0
+    o = oracle.OracleSim(sc, rho=np.array([rho_i]))
+    p_i = 1.0 * (rho_i - 1000.0)
+    w = o.wall()
+    p_w, rho_w = w["pw"][0], w["rhow"][0, 0]
+    assert p_w == pytest.approx(p_i + rho_i * 9.81 * z, rel=1e-12)
+    assert rho_w == pytest.approx(1000.0 + p_w, rel=1e-12)
+    e = 1e-7 * h
+    dWdr = (oracle.W(z + e, h) - oracle.W(z - e, h)) / (2 * e)
+    m_w = 1000.0 * dp ** 3
+    a_z = o.fluid()["a"][0, 2]
+    p_star = (a_z + 9.81) * rho_i * rho_w / (-2.0 * m_w * dWdr)
+    assert p_star == pytest.approx((rho_w * p_i + rho_i * p_w) / (rho_i + rho_w), rel=1e-7)
+
 @pytest.mark.parametrize("eos", ["tait", "linear"])
 def test_wall_density_is_kept_at_half_the_reference(eos):
     """Below EOS(rho0/2) the wall density is rho0/2 (the Tait inverse has no
@@ -314,6 +365,42 @@ def test_continuity_pressure_diffusion_sign():
     assert drho[centre] < 0
     f, _ = oracle.OracleSim(sc, rho=rho).neighbors(centre)
     assert np.all(drho[f] > 0)
+
+
+def _pair_scene(x_j, v_i, v_j, phases, phase_j, c0=10.0, g=(0.0, 0.0, 0.0), walls=None):
+    """Fluid particle 0 at the origin and particle 1 at x_j, no walls unless
+    given; reinitialisation off."""
+    dp = 0.01
+    fluid = np.array([[0.0, 0.0, 0.0], x_j])
+    wall = np.zeros((0, 3)) if walls is None else np.asarray(walls, float)
+    return S.Scene(name="pair", dp=dp, h=1.3 * dp, c0=c0, g=g, lo=(-0.05, -0.05, -0.05),
+                   hi=(0.05, 0.05, 0.05), phases=phases, fluid_pos=fluid,
+                   fluid_vel=np.array([v_i, v_j], float), fluid_phase=np.array([0, phase_j], np.int32),
+                   wall_pos=wall, reinit_every=0)
+
+
+def test_continuity_contact_at_an_interface_moves_with_the_mass_weighted_velocity():
+    """Two particles of different phases (rho0 1000 and 500, both at their
+    reference density, so at equal pressure) approaching head-on.  At equal
+    pressures the Riemann solution of Eq. (RSsolution) puts the contact at
+    the density-weighted mean normal velocity, so each particle compresses
+    with U_L - U* = rho_R (U_L - U_R) / (rho_L + rho_R): the logarithmic
+    density rates stand in the ratio m_j : m_i of the particle masses (here
+    1 : 2), whatever the densities.  With the densities of the mixture
+    swapped the ratio would be m_j rho_i^2 : m_i rho_j^2 (2 : 1)."""
+    phases = [S.Phase(eos="linear", rho0=1000.0, reinit="none"),
+              S.Phase(eos="linear", rho0=500.0, reinit="none")]
+    u = 0.2
+    sc = _pair_scene([0.011, 0.0, 0.0], [u, 0.0, 0.0], [-u, 0.0, 0.0], phases, 1)
+    rho = np.array([1000.0, 500.0])
+    drho, _ = oracle.OracleSim(sc, rho=rho).rates()
+    assert drho[0] > 0 and drho[1] > 0  # both compress
+    assert (drho[0] / rho[0]) / (drho[1] / rho[1]) == pytest.approx(500.0 / 1000.0, rel=1e-12)
+    # one phase (equal masses): equal logarithmic rates at unequal densities
+    # would need unequal pressures; at equal densities the rates are equal
+    sc1 = _pair_scene([0.011, 0.0, 0.0], [u, 0.0, 0.0], [-u, 0.0, 0.0], phases[:1], 0)
+    d1, _ = oracle.OracleSim(sc1, rho=np.array([1000.0, 1000.0])).rates()
+    assert d1[0] == pytest.approx(d1[1], rel=1e-14)
 
 
 # ---------------------------------------------------------------- momentum
@@ -501,6 +588,32 @@ def test_time_step_limits():
     sc.c0 = 0.2   # below sqrt(g h): the body-force limit wins
     dt2 = oracle.OracleSim(sc).step(1)
     assert dt2 == pytest.approx(0.25 * math.sqrt(sc.h / G), rel=1e-14)
+    # the flow speed enters the acoustic limit: a blob translating at
+    # |v| = 3 m/s without gravity
+    blob = S.jittered_blob(n=(4, 4, 4), vel_scale=0.0)
+    blob.g = (0.0, 0.0, 0.0)
+    v = np.array([1.0, -2.0, 2.0])
+    blob.fluid_vel = np.tile(v, (blob.n_fluid, 1))
+    dt3 = oracle.OracleSim(blob, rho=np.full(blob.n_fluid, 1000.0)).step(1)
+    assert dt3 == pytest.approx(0.25 * blob.h / (blob.c0 + 3.0), rel=1e-14)
+
+
+def test_diagnostics_of_a_translating_blob():
+    """Sec. 4.1's energies on a blob of N particles of mass m = rho0 dx^3
+    translating at v: mass N m, momentum N m v, kinetic energy N m |v|^2 / 2,
+    potential energy -N m g . x_mean, U_max = |v|, nothing escaped."""
+    blob = S.jittered_blob(n=(5, 4, 3), vel_scale=0.0)
+    v = np.array([0.3, -0.4, 1.2])
+    blob.fluid_vel = np.tile(v, (blob.n_fluid, 1))
+    o = oracle.OracleSim(blob, rho=np.full(blob.n_fluid, 1000.0))
+    d = o.diagnostics()
+    N, m = blob.n_fluid, 1000.0 * blob.dp ** 3
+    g = np.array(blob.g, float)
+    assert d[0] == pytest.approx(N * m, rel=1e-13)
+    assert np.allclose(d[1:4], N * m * v, rtol=1e-13, atol=0)
+    assert d[4] == pytest.approx(0.5 * N * m * (v @ v), rel=1e-13)
+    assert d[5] == pytest.approx(-N * m * (g @ blob.fluid_pos.mean(0)), rel=1e-12)
+    assert d[6] == pytest.approx(np.sqrt(v @ v), rel=1e-14) and d[7] == 0.0
 
 
 # ---------------------------------------------------------- whole-step checks
