@@ -75,6 +75,28 @@ def test_torch_step_matches_c_oracle(nsteps):
     assert rel(St["sigma"].numpy(), o["sigma"]) < 1e-12
 
 
+def test_torch_wall_density_floor_matches_c_oracle():
+    """Fluid torn to 0.3 rho0 under a roof: the extrapolated p_w of the walls
+    above it falls below EOS(rho0/2), where both restatements hold the wall
+    density at rho0/2 (and use the inverse EOS elsewhere)."""
+    dp = 0.01
+    xw = np.array([[i * dp, j * dp, dp] for i in (-1, 0, 1) for j in (-1, 0, 1)])
+    sc = S.Scene(name="torn", dp=dp, h=1.3 * dp, c0=10.0, g=(0.0, 0.0, -9.81), lo=(-0.1, -0.1, -0.1),
+                 hi=(0.1, 0.1, 0.1), phases=[S.Phase(rho0=1000.0, eos="tait", z_top=0.0)],
+                 fluid_pos=np.zeros((1, 3)), fluid_vel=np.zeros((1, 3)),
+                 fluid_phase=np.zeros(1, np.int32), wall_pos=xw)
+    rho0 = np.array([300.0])
+    ref = c_oracle(sc, rho0)
+    ow = ref.wall()
+    P = A.params_from_scene(sc, ow["normal"], ref.sigma0)
+    t = lambda a: torch.tensor(np.asarray(a, np.float64))  # noqa: E731
+    St = A.run(t(sc.fluid_pos), t(sc.fluid_vel), t(rho0), P, t(sc.c0), t(sc.gamma_p),
+               t(sc.phases[0].mu), 0, DT)
+    assert (ow["rhow"][:, 0] == 500.0).any()
+    assert np.allclose(St["pw"].numpy(), ow["pw"], rtol=1e-12, atol=0)
+    assert np.allclose(St["rhow"].numpy().reshape(len(xw), -1)[:, 0], ow["rhow"][:, 0], rtol=1e-12, atol=0)
+
+
 def _loss(sc, rho0, normals, sigma0, seed, nsteps, x=None, v=None, r=None, c0=None, gp=None,
           mu=None):
     P = A.params_from_scene(sc, normals, sigma0)

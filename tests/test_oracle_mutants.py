@@ -3,12 +3,16 @@ mistake in a copy of the oracle's C source (a dropped term, a wrong sign,
 factor or exponent, transposed operands, a wrong index order), builds that
 copy on the CPU, and runs the oracle's pin files against it in a subprocess
 (``SPH_ORACLE_LIB`` makes ``oracle.lib()`` load the copy).  Every mistake
-must make at least one pin fail.  The product code is not involved; the
+must make at least one pin fail.  The same is done for the reference
+adjoint's PyTorch restatement of the step (``oracle/adjoint.py``): a copy of
+the ``oracle`` package with one mistake in it, in a temporary tree, against
+``tests/test_adjoint_oracle.py``.  The product code is not involved; the
 mistakes exist only in temporary copies.
 
 A case whose original text no longer occurs exactly once in the oracle
 fails, so the list follows the source."""
 import os
+import shutil
 import subprocess
 import sys
 
@@ -169,5 +173,99 @@ def test_a_planted_mistake_fails_a_pin(workdir, name, original, mistaken):
     subprocess.check_call(oracle.compile_command(str(c_file), str(so_file)))
     run = subprocess.run([sys.executable, "-m", "pytest", *PIN_FILES, "-x", "-q", "-p", "no:cacheprovider"],
                          cwd=ROOT, env=dict(os.environ, SPH_ORACLE_LIB=str(so_file)),
+                         capture_output=True, text=True, timeout=600)
+    assert run.returncode == 1, f"no pin caught: {name}\n{run.stdout[-2000:]}"
+
+
+# (what the mistake is, original text, mistaken text) in oracle/adjoint.py
+ADJOINT_MUTANTS = [
+    ('kernel normalisation',
+     'return 21.0 / (16.0 * math.pi * h ** 3) * t ** 4 * (2.0 * q + 1.0)',
+     'return 21.0 / (15.0 * math.pi * h ** 3) * t ** 4 * (2.0 * q + 1.0)'),
+    ('dW/dr sign',
+     'return -5.0 * 21.0 / (16.0 * math.pi * h ** 3) * q * t ** 3 / h',
+     'return 5.0 * 21.0 / (16.0 * math.pi * h ** 3) * q * t ** 3 / h'),
+    ('Tait exponent',
+     '((rho / P.rho0) ** P.gamma_tait - 1.0)',
+     '((rho / P.rho0) ** (P.gamma_tait - 1.0) - 1.0)'),
+    ('Riemann U* sign',
+     'Ustar = U_bar + 0.5 * (pL - pR) / (c * rho_bar)',
+     'Ustar = U_bar + 0.5 * (pR - pL) / (c * rho_bar)'),
+    ('limiter factor',
+     'beta = torch.minimum(3.0 * torch.clamp(UL - UR, min=0.0), c * torch.ones_like(UL))',
+     'beta = torch.minimum(2.0 * torch.clamp(UL - UR, min=0.0), c * torch.ones_like(UL))'),
+    ('P_bar operands',
+     'P_bar = (rhoL * pR + rhoR * pL) / rs',
+     'P_bar = (rhoL * pL + rhoR * pR) / rs'),
+    ('mixture transposed',
+     'vmix = (rho[i][:, None] * v_i + rho_j[:, None] * v_j) / (rho[i] + rho_j)[:, None]',
+     'vmix = (rho_j[:, None] * v_i + rho[i][:, None] * v_j) / (rho[i] + rho_j)[:, None]'),
+    ('continuity factor 2',
+     'out.index_add_(0, i, 2.0 * rho[i] * (m / rho_j) * dot)',
+     'out.index_add_(0, i, rho[i] * (m / rho_j) * dot)'),
+    ('wall hydrostatic sign',
+     '(p[wi] + rho[wi] * (rwf @ P.g)) * Wk',
+     '(p[wi] - rho[wi] * (rwf @ P.g)) * Wk'),
+    ('wall density floor',
+     'p_half = eos_p(0.5 * P.rho0 * torch.ones_like(pw), P, c0)',
+     'p_half = eos_p(0.4 * P.rho0 * torch.ones_like(pw), P, c0)'),
+    ('momentum rho_j -> rho_i',
+     'a = a.index_add(0, fi, (-2.0 * m * pstar / (rho[fi] * rho[fj]))[:, None] * gw)',
+     'a = a.index_add(0, fi, (-2.0 * m * pstar / (rho[fi] * rho[fi]))[:, None] * gw)'),
+    ('wall p* operands',
+     'pstar = (rho_i * p_w + rho_w * p_i) / (rho_i + rho_w)',
+     'pstar = (rho_i * p_i + rho_w * p_w) / (rho_i + rho_w)'),
+    ('viscosity sign',
+     'a = a.index_add(0, fi, kv[:, None] * (v[fi] - v[fj]))',
+     'a = a.index_add(0, fi, kv[:, None] * (v[fj] - v[fi]))'),
+    ('wall viscosity dropped',
+     'a = a.index_add(0, wi, kv[:, None] * v[wi])',
+     'a = a.index_add(0, wi, 0.0 * kv[:, None] * v[wi])'),
+    ('penalty lambda power',
+     'lam = torch.where(act, (1.0 - delta) ** 2 / dx, torch.zeros_like(delta))',
+     'lam = torch.where(act, (1.0 - delta) / dx, torch.zeros_like(delta))'),
+    ('penalty delta factor',
+     'delta = 2.0 * r / dx * torch.abs(en)',
+     'delta = r / dx * torch.abs(en)'),
+    ('reinit factor',
+     'return rho_num + torch.clamp(rho - rho_num, min=0.0) * P.rho0 / rho',
+     'return rho_num + torch.clamp(rho - rho_num, min=0.0)'),
+    ('first kick full',
+     'vh = S["v"] + 0.5 * dt * S["a"]',
+     'vh = S["v"] + dt * S["a"]'),
+    ('second kick full',
+     'v1 = vh + 0.5 * dt * a',
+     'v1 = vh + dt * a'),
+    ('continuity at old densities',
+     'a = momentum(x, vh, rho1, p1, pw, rhow, P, c0, gamma_p, mu, pairs)',
+     'a = momentum(x, vh, rho, p, pw, rhow, P, c0, gamma_p, mu, pairs)'),
+    ('nearest image',
+     'k = torch.where(P.period > 0, torch.round(r.detach() / L), torch.zeros_like(r))',
+     'k = torch.where(P.period > 0, torch.floor(r.detach() / L), torch.zeros_like(r))'),
+    ('number density self term',
+     's = torch.full((n,), float(W(torch.tensor(0.0, dtype=F64), P.h)), dtype=F64)',
+     's = torch.zeros((n,), dtype=F64)'),
+]
+
+
+@pytest.mark.parametrize("name,original,mistaken", ADJOINT_MUTANTS, ids=[m[0] for m in ADJOINT_MUTANTS])
+def test_a_planted_mistake_in_the_reference_adjoint_fails_a_pin(tmp_path, name, original, mistaken):
+    pytest.importorskip("torch")
+    pytest.importorskip("scipy")
+    with open(os.path.join(ROOT, "oracle", "adjoint.py")) as fh:
+        src = fh.read()
+    assert src.count(original) == 1, f"the text of case {name!r} no longer occurs once in the adjoint"
+    tree = tmp_path / "tree"
+    shutil.copytree(os.path.join(ROOT, "oracle"), tree / "oracle",
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    (tree / "oracle" / "adjoint.py").write_text(src.replace(original, mistaken))
+    os.symlink(os.path.join(ROOT, "paper_2110_02621_gb300"), tree / "paper_2110_02621_gb300")
+    (tree / "tests").mkdir()
+    for f in ("conftest.py", "test_adjoint_oracle.py"):
+        shutil.copy(os.path.join(ROOT, "tests", f), tree / "tests" / f)
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), tree / "pytest.ini")
+    run = subprocess.run([sys.executable, "-m", "pytest", "tests/test_adjoint_oracle.py", "-x", "-q",
+                          "-p", "no:cacheprovider"],
+                         cwd=tree, env=dict(os.environ, SPH_ORACLE_LIB=oracle.build()),
                          capture_output=True, text=True, timeout=600)
     assert run.returncode == 1, f"no pin caught: {name}\n{run.stdout[-2000:]}"

@@ -246,7 +246,6 @@ def torn_fluid_under_a_roof(eos="tait"):
     return sc, np.array([300.0])
 
 
-
 def test_wall_pressure_of_two_phases_leaves_out_the_heavy_phase():
     """Sec. 2.3: in multi-phase flow the extrapolation weights are divided by
     the fluid density so that the heavy phase's contribution vanishes.  A wall
