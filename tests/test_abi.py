@@ -86,3 +86,98 @@ def test_create_rejects_bad_arguments_without_touching_the_gpu(lib):
     assert sph.sph_create(P, F3, None)[0] == sph.SPH_ERR_ARG
     assert lib.sph_step(None, 1, 0.0, None) == sph.SPH_ERR_ARG
     lib.sph_destroy(None)
+
+
+def _p_set(**kw):
+    def f(P, F, W, keep):
+        for k, v in kw.items():
+            setattr(P, k, v)
+    return f
+
+
+def _phase_set(**kw):
+    def f(P, F, W, keep):
+        for k, v in kw.items():
+            setattr(P.phase[0], k, v)
+    return f
+
+
+def _axis(field, d, value):
+    def f(P, F, W, keep):
+        getattr(P, field)[d] = value
+    return f
+
+
+def _fluid_array(name, value, row=0, col=0):
+    def f(P, F, W, keep):
+        import numpy as np
+        a = np.array(keep[name], dtype=keep[name].dtype, copy=True)
+        if a.ndim == 2:
+            a[row, col] = value
+        else:
+            a[row] = value
+        keep[name + "_bad"] = a
+        setattr(F, name, a.ctypes.data)
+    return f
+
+
+def _periodic_box_axis(P, F, W, keep):
+    P.periodic = 1
+    P.hi[0] = P.lo[0] + 2 * P.h * 4.3  # 4.3 cells: not whole
+
+
+def _tiny_cells(P, F, W, keep):
+    P.h = 1e-4  # 2h cells of 0.2 mm over a 0.1 m box: ~1.3e8 cells
+
+
+def _two_d_periodic_y(P, F, W, keep):
+    P.dim = 2
+    P.periodic = 2
+
+
+REJECTIONS = [
+    ("h <= 0", _p_set(h=-1.0), "must be finite and > 0"),
+    ("c0 = 0", _p_set(c0=0.0), "must be finite and > 0"),
+    ("cfl nan", _p_set(cfl=float("nan")), "must be finite and > 0"),
+    ("gamma_p < 0", _p_set(gamma_p=-0.1), "gamma_p >= 0"),
+    ("g inf", _axis("g", 2, float("inf")), "g, lo, hi must be finite"),
+    ("hi <= lo", _axis("hi", 1, -1.0), "hi must exceed lo"),
+    ("n_phases 0", _p_set(n_phases=0), "n_phases must be 1 or 2"),
+    ("reinit_every < 0", _p_set(reinit_every=-1), "reinit_every"),
+    ("precision", _p_set(precision=7), "unknown precision"),
+    ("dim 1", _p_set(dim=1), "dim must be"),
+    ("rho0 <= 0", _phase_set(rho0=0.0), "phase rho0"),
+    ("mu < 0", _phase_set(mu=-1.0), "phase rho0"),
+    ("eos 2", _phase_set(eos=2), "out of range"),
+    ("reinit 3", _phase_set(reinit=3), "out of range"),
+    ("periodic mask", _p_set(periodic=8), "periodic is a mask"),
+    ("2-D periodic y", _two_d_periodic_y, "y cannot be periodic"),
+    ("fractional period", _periodic_box_axis, "whole number"),
+    ("too many cells", _tiny_cells, "too many cells"),
+    ("fluid n < 0", lambda P, F, W, keep: setattr(F, "n", -1), "fluid.n"),
+    ("fluid pos NULL", lambda P, F, W, keep: setattr(F, "pos", None), "fluid.pos"),
+    ("wall pos NULL", lambda P, F, W, keep: setattr(W, "pos", None), "wall.pos"),
+    ("fluid velocity nan", _fluid_array("vel", float("nan"), 1, 2), "velocity"),
+    ("fluid rho <= 0", _fluid_array("rho", 0.0, 2), "rho must be > 0"),
+    ("fluid phase out of range", _fluid_array("phase", 1, 3), "phase out of range"),
+]
+
+
+@pytest.mark.parametrize("what,spoil,message", REJECTIONS, ids=[r[0] for r in REJECTIONS])
+def test_each_validation_rule_refuses_before_any_cuda_call(lib, what, spoil, message):
+    """Every rule of sph_create's validation returns SPH_ERR_ARG with its own
+    message, no context, and no CUDA call (so it runs here, without a GPU)."""
+    import numpy as np
+    from paper_2110_02621_gb300 import scenes
+    sc = scenes.still_water_tank(n_fluid=(3, 3, 3))
+    P = sph.make_params(sc)
+    keep = {"pos": np.ascontiguousarray(sc.fluid_pos), "vel": np.zeros((sc.n_fluid, 3)),
+            "rho": np.full(sc.n_fluid, 1000.0), "phase": np.zeros(sc.n_fluid, np.int32),
+            "wall": np.ascontiguousarray(sc.wall_pos)}
+    F = sph.sph_fluid(sc.n_fluid, keep["pos"].ctypes.data, keep["vel"].ctypes.data, keep["rho"].ctypes.data,
+                      keep["phase"].ctypes.data)
+    W = sph.sph_wall(len(keep["wall"]), keep["wall"].ctypes.data)
+    spoil(P, F, W, keep)
+    st, ctx = sph.sph_create(P, F, W)
+    assert st == sph.SPH_ERR_ARG and not ctx.value, what
+    assert message in sph.sph_last_error(None), (what, sph.sph_last_error(None))
