@@ -150,6 +150,18 @@ MUTANTS = [
     ('penalty side',
      'double Ppen = s->P.gamma_p * lambda * fabs(p_i * en);',
      'double Ppen = s->P.gamma_p * lambda * p_i * en;'),
+    ('2-D normalisation',
+     'return dim == 2 ? 7.0 / (4.0 * PI * h * h) :',
+     'return dim == 2 ? 7.0 / (3.0 * PI * h * h) :'),
+    ('2-D lattice sum',
+     'int KY = dim == 2 ? 0 : K;',
+     'int KY = K;'),
+    ('gauge phase filter',
+     'if (!in_grid(s, j) || s->phase[j] != 0) continue;',
+     'if (!in_grid(s, j)) continue;'),
+    ('gauge top sample',
+     'int64_t K = (int64_t)floor((zhi - zlo) / dz);',
+     'int64_t K = (int64_t)floor((zhi - zlo) / dz) - 1;'),
 ]
 
 
