@@ -155,6 +155,8 @@ REJECTIONS = [
     ("fractional period", _periodic_box_axis, "whole number"),
     ("too many cells", _tiny_cells, "too many cells"),
     ("fluid n < 0", lambda P, F, W, keep: setattr(F, "n", -1), "fluid.n"),
+    ("fluid n = 2^26", lambda P, F, W, keep: setattr(F, "n", 1 << 26), "fluid.n"),
+    ("wall n = 2^26", lambda P, F, W, keep: setattr(W, "n", 1 << 26), "wall.n"),
     ("fluid pos NULL", lambda P, F, W, keep: setattr(F, "pos", None), "fluid.pos"),
     ("wall pos NULL", lambda P, F, W, keep: setattr(W, "pos", None), "wall.pos"),
     ("fluid velocity nan", _fluid_array("vel", float("nan"), 1, 2), "velocity"),
