@@ -162,6 +162,33 @@ MUTANTS = [
     ('gauge top sample',
      'int64_t K = (int64_t)floor((zhi - zlo) / dz);',
      'int64_t K = (int64_t)floor((zhi - zlo) / dz) - 1;'),
+    ('body force at t^n',
+     '    s->t += dt;\n    body_force(s, s->t);',
+     '    body_force(s, s->t);\n    s->t += dt;'),
+    ('reinit phase of the cycle',
+     's->step % s->P.reinit_every == 0) reinit_density(s);',
+     's->step % s->P.reinit_every == 1) reinit_density(s);'),
+    ('periodic cell key wrap dropped',
+     '            if (c[d] >= s->nc[d]) c[d] -= s->nc[d];\n',
+     ''),
+    ('linear EOS c^2',
+     'return c0 * c0 * (rho - ph->rho0);',
+     'return c0 * (rho - ph->rho0);'),
+    ('summation without walls',
+     '    for_neighbors(s, s->x + 3 * i, s->xw, s->order_w, s->start_w, sum_visit_w, &c);\n',
+     ''),
+    ('sigma without walls',
+     '    for_neighbors(s, s->x + 3 * i, s->xw, s->order_w, s->start_w, sigma_visit_w, &c);\n',
+     ''),
+    ('stencil x range',
+     '            for (int dx = -1; dx <= 1; dx++) {',
+     '            for (int dx = -1; dx <= 0; dx++) {'),
+    ('periodic stencil wrap',
+     'if (is_periodic(s, d)) q[d] = (q[d] + s->nc[d]) % s->nc[d];',
+     'if (is_periodic(s, d)) q[d] = q[d] % s->nc[d];'),
+    ('self pair kept',
+     'if (r2 >= rc2 || r2 == 0.0) continue; /* self and r = 0 skipped */',
+     'if (r2 >= rc2) continue; /* self and r = 0 skipped */'),
 ]
 
 

@@ -100,6 +100,23 @@ def test_a_lone_particle_wraps_around_the_period():
     assert t * abs(v[0]) > L[0]  # crossed the lower x face at least once
 
 
+def test_a_particle_just_below_the_upper_face_stays_in_the_grid():
+    """A position one ulp below hi along a periodic axis divides to exactly
+    the cell count in floating point; the binning wraps that cell to 0, so the
+    particle stays inside the grid and sees its neighbour across the face."""
+    box = S.periodic_box(m=(3, 1, 1), dp=0.025)  # a box where x / cs rounds up to the cell count
+    L = np.array(box.hi) - np.array(box.lo)
+    a = [np.nextafter(box.hi[0], -np.inf), 0.5 * L[1], 0.5 * L[2]]
+    b = [0.3 * box.dp, 0.5 * L[1], 0.5 * L[2]]
+    sc = dataclasses.replace(box, fluid_pos=np.array([a, b]), fluid_vel=np.zeros((2, 3)),
+                             fluid_phase=np.zeros(2, np.int32), rho_init=None, g=(0.0, 0.0, 0.0))
+    assert np.floor((a[0] - box.lo[0]) / (2 * box.h)) == round(L[0] / (2 * box.h))  # the rounding case
+    o = oracle.OracleSim(sc, rho=np.full(2, 1000.0))
+    assert o.diagnostics()[7] == 0.0
+    f, _ = o.neighbors(0)
+    assert list(f) == [1]
+
+
 def test_a_period_must_be_whole_cells():
     sc = S.periodic_box()
     bad = dataclasses.replace(sc, hi=(sc.hi[0] + 0.3 * sc.dp, sc.hi[1], sc.hi[2]))

@@ -559,6 +559,26 @@ def test_summation_density_lattice():
     assert np.allclose(f["rho"][inner], 1000.0 * sc.dp ** 3 * o.sigma0, rtol=1e-12)
 
 
+def test_summation_density_is_completed_by_the_walls():
+    """The wall dummy particles continue the fluid lattice (three layers, the
+    first dx/2 behind each face), so they complete the kernel support of the
+    fluid next to them: in a still-water tank with summation density every
+    particle more than 2h below the free surface, those touching the floor, the
+    side walls and the corners included, has the interior lattice value
+    rho = m sigma^0 of Eq. (densitySummation)."""
+    sc = S.still_water_tank(n_fluid=(8, 8, 8), eos="linear")
+    sc.phases[0].density = "summation"
+    sc.phases[0].reinit = "none"
+    o = oracle.OracleSim(sc, rho=np.full(sc.n_fluid, 1000.0))
+    o.step(1, dt=1e-7)
+    f = o.fluid()
+    H = sc.phases[0].z_top
+    deep = sc.fluid_pos[:, 2] < H - 2 * sc.h
+    at_wall = deep & ((sc.fluid_pos[:, 2] < sc.dp) | (sc.fluid_pos[:, 0] < sc.dp))
+    assert at_wall.sum() > 20
+    assert np.allclose(f["rho"][deep], 1000.0 * sc.dp ** 3 * o.sigma0, rtol=1e-9)
+
+
 # -------------------------------------------------------------- integrator
 def test_kick_drift_kick_free_fall():
     """A lone particle under gravity: KDK is exact for constant acceleration,
