@@ -214,6 +214,30 @@ def test_torch_step_matches_c_oracle_with_periodic_axes(name):
         assert rel(St["pw"].numpy(), ow["pw"]) < 1e-9
 
 
+def test_torch_lone_particle_wraps_like_the_c_oracle():
+    """A lone particle crossing the lower x face of a periodic box: both
+    restatements wrap its drifted position back into [lo, hi), to the same
+    value, (x0 + v t) modulo the period."""
+    import dataclasses
+    box = S.periodic_box()
+    L = np.array(box.hi) - np.array(box.lo)
+    x0 = np.array([[0.02 * L[0], 0.5 * L[1], 0.5 * L[2]]])
+    v0 = np.array([[-0.5, 0.2, 0.0]])
+    sc = dataclasses.replace(box, fluid_pos=x0, fluid_vel=v0, fluid_phase=np.zeros(1, np.int32), rho_init=None,
+                             g=(0.0, 0.0, 0.0))
+    rho0 = np.array([1000.0])
+    ref = c_oracle(sc, rho0)
+    P = A.params_from_scene(sc, ref.wall()["normal"], ref.sigma0)
+    t = lambda a: torch.tensor(np.asarray(a, np.float64))  # noqa: E731
+    dt, n = 1e-3, 20
+    St = A.run(t(x0), t(v0), t(rho0), P, t(sc.c0), t(sc.gamma_p), t(sc.phases[0].mu), n, dt)
+    ref.step(n, dt)
+    xt, xc = St["x"].numpy()[0], ref.fluid()["x"][0]
+    assert x0[0, 0] + v0[0, 0] * n * dt < 0.0  # it crossed
+    expect = np.array(box.lo) + np.mod(x0[0] + v0[0] * n * dt - np.array(box.lo), L)
+    assert np.allclose(xt, expect, rtol=0, atol=1e-13) and np.allclose(xc, expect, rtol=0, atol=1e-13)
+
+
 def test_periodic_autograd_matches_central_differences():
     sc = periodic_scenes()["box"]
     _, rho0, normals, sigma0 = setup(sc)

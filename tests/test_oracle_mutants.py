@@ -284,6 +284,24 @@ ADJOINT_MUTANTS = [
     ('number density self term',
      's = torch.full((n,), float(W(torch.tensor(0.0, dtype=F64), P.h)), dtype=F64)',
      's = torch.zeros((n,), dtype=F64)'),
+    ('reinit cycle',
+     'P.reinit_every > 0 and n % P.reinit_every == 0)',
+     'P.reinit_every > 0 and n % P.reinit_every == 1)'),
+    ('no wrap after drift',
+     'x = wrap(S["x"] + dt * vh, P)',
+     'x = S["x"] + dt * vh'),
+    ('wall pressure at old density',
+     'pw, rhow = wall_pressure(x, rho1, p1, P, c0, pairs[1], nw)',
+     'pw, rhow = wall_pressure(x, rho, p, P, c0, pairs[1], nw)'),
+    ('sigma at old positions',
+     'sigma = number_density(x, P, pairs, x.shape[0])\n    return {"x": x, "v": v1',
+     'sigma = number_density(S["x"], P, pairs, x.shape[0])\n    return {"x": x, "v": v1'),
+    ('continuity with v^n',
+     'drdt = continuity(x, vh, rho, p, S["pw"], S["rhow"], P, c0, pairs)',
+     'drdt = continuity(x, S["v"], rho, p, S["pw"], S["rhow"], P, c0, pairs)'),
+    ('number density without walls',
+     '    return s.index_add(0, wi, W(r, P.h))',
+     '    return s'),
 ]
 
 
