@@ -14,6 +14,10 @@ namespace sph {
 
 int32_t scan_blocks(int64_t n);
 int64_t scan_max_len();
+// Cell count of a dims[0] x dims[1] x dims[2] grid, or -1 when an extent is
+// below 1 or the grid holds more cells than the scan takes (scan_max_len() - 2).
+// Each extent is checked before it is multiplied in, so no product overflows.
+int64_t grid_cell_count(const int32_t dims[3]);
 // out[0..n] = exclusive prefix sums of in[0..n-1] (out[n] = total);
 // sums needs scan_blocks(n) entries; clear (NULL or in) is zeroed behind the
 // scan.  Returns the number of kernels launched.
@@ -38,6 +42,8 @@ struct SimBase {
     virtual sph_status get_state(const sph_state_out& o, int32_t where) = 0;
     virtual sph_status get_cells(uint32_t* kf, int32_t* of, int32_t* sf, uint32_t* kw, int32_t* ow,
                                  int32_t* sw) = 0;
+    virtual sph_status get_neighbors(int64_t* f_off, int32_t* f_ids, int64_t f_cap, int64_t* w_off,
+                                     int32_t* w_ids, int64_t w_cap, int64_t overflow[2]) = 0;
     virtual sph_status diagnostics(double out[8]) = 0;
     virtual sph_status diagnostics_async(double* out, int32_t where) = 0;
     virtual sph_status counters(int64_t* steps, int64_t* active) = 0;

@@ -47,12 +47,8 @@ extern "C" sph_status sph_bin_sort_noalloc(const double* pos, int64_t n, const d
 {
     if (n < 0 || n > 2000000000 || !lo || !dims || !(h > 0) || !start || (n > 0 && (!pos || !key || !order)))
         return SPH_ERR_ARG;
-    int64_t n_cells = 1;
-    for (int d = 0; d < 3; ++d) {
-        if (dims[d] < 1) return SPH_ERR_ARG;
-        n_cells *= dims[d];
-    }
-    if (n_cells > sph::scan_max_len() - 2) return SPH_ERR_ARG;
+    const int64_t n_cells = sph::grid_cell_count(dims);
+    if (n_cells < 0) return SPH_ERR_ARG;
     const sph::BinSortScratch L = sph::bin_sort_scratch_layout(n, n_cells);
     if (L.bytes > kScratchBytes) return SPH_ERR_CAPACITY;
     void* scratch = nullptr;

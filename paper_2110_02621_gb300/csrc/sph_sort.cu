@@ -141,6 +141,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(const int32_t* in,
 int32_t scan_blocks(int64_t n) { return (int32_t)((n + SCAN_TILE - 1) / SCAN_TILE); }
 int64_t scan_max_len() { return SCAN_MAX; }
 
+int64_t grid_cell_count(const int32_t dims[3])
+{
+    int64_t n = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (dims[d] < 1 || dims[d] > SCAN_MAX) return -1;
+        n *= dims[d];  // <= 2^24 * 2^24: no overflow
+        if (n > SCAN_MAX - 2) return -1;
+    }
+    return n;
+}
+
 int scan_exclusive(const int32_t* in, int32_t n, int32_t* out, int32_t* sums, cudaStream_t st, int32_t* clear)
 {
     if (n <= SCAN_SMALL) {

@@ -183,3 +183,19 @@ def test_each_validation_rule_refuses_before_any_cuda_call(lib, what, spoil, mes
     st, ctx = sph.sph_create(P, F, W)
     assert st == sph.SPH_ERR_ARG and not ctx.value, what
     assert message in sph.sph_last_error(None), (what, sph.sph_last_error(None))
+
+
+@pytest.mark.parametrize("dims", [(1 << 21, 1 << 21, 1 << 22), (2**31 - 1, 2**31 - 1, 2**31 - 1),
+                                  (1 << 12, 1 << 12, 1), (0, 5, 5), (5, -3, 5)],
+                         ids=["product_wraps_to_zero", "int32_max_extents", "one_cell_too_many",
+                              "zero_extent", "negative_extent"])
+@pytest.mark.parametrize("fn", ["sph_bin_sort", "sph_bin_sort_noalloc"])
+def test_binning_refuses_grids_beyond_the_scan(lib, fn, dims):
+    """A grid of more cells than the scan takes (2^24 - 2), or whose cell count
+    would overflow a 64-bit product of the extents (2^21 x 2^21 x 2^22 wraps to
+    0), or with an extent below 1, is refused with SPH_ERR_ARG before any
+    launch: the pointers below are never dereferenced, so this runs without a
+    GPU."""
+    dummy = 1 << 20  # never dereferenced: validation comes first
+    st = getattr(sph, fn)(dummy, 10, (0.0, 0.0, 0.0), 0.013, dims, dummy, dummy, dummy, 0)
+    assert st == sph.SPH_ERR_ARG

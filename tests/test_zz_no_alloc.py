@@ -46,11 +46,17 @@ def test_noalloc_matches_allocating_binning_twice(torch_cuda):
     h = 0.013
     cs = 2 * h
     rng = np.random.default_rng(2110)
+    # the first two grids (6,552 and 2,744 cells) take the one-block scan; the
+    # third (98 x 78 x 73 = 558,012 cells, more than 512 blocks of 1,024) the
+    # reduce / scan-of-sums / down-sweep kernels and the block-sums part of the
+    # fixed scratch
     inputs = [rng.uniform(0, 1, (30011, 3)) * [0.6, 0.4, 0.3],
-              rng.integers(0, 12, (9001, 3)) * cs + rng.uniform(0, cs, (9001, 3)) * (rng.uniform(size=(9001, 1)) < 0.5)]
-    for x in inputs:  # two calls in a row: the second reuses the scratch of the first
+              rng.integers(0, 12, (9001, 3)) * cs + rng.uniform(0, cs, (9001, 3)) * (rng.uniform(size=(9001, 1)) < 0.5),
+              rng.uniform(0, 1, (200003, 3)) * [96 * cs, 76 * cs, 71 * cs]]
+    for x in inputs:  # calls in a row: each reuses the scratch of the one before
         lo = (0.0, 0.0, 0.0)
         dims = tuple(int(np.ceil((x[:, d].max() + 2 * cs) / cs)) for d in range(3))
+        assert int(np.prod(dims)) in (6552, 2744, 558012)
         ref = _bin(torch, sph.sph_bin_sort, x, lo, h, dims)
         got = _bin(torch, sph.sph_bin_sort_noalloc, x, lo, h, dims)
         assert ref[0] == sph.SPH_OK and got[0] == sph.SPH_OK
