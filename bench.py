@@ -41,24 +41,36 @@ WORKLOAD = "dam_break_80k"
 
 # Algorithmic floating-point operations per in-support pair (add, sub, mul,
 # div, sqrt = 1; fma = 2), counted from the pair formulas as the kernels
-# evaluate them.
+# evaluate them.  The 27-cell candidate tests of the neighbour search are not
+# algorithmic work (a different search visits fewer candidates) and are not
+# counted.
 FLOPS_PAIR = {
     "momentum_ff": 50,      # Riemann p*, limiter, pressure force, sigma
     "momentum_fw": 40,      # Eq. (RSatWall) pressure force, sigma (penalty rarely active)
     "continuity_ff": 36,    # Riemann continuity term
     "continuity_fw": 33,
     "wall_pressure": 24,    # extrapolation sums
-    "neighbors": 11,        # per 27-cell candidate: r (6) and |r|^2 (5)
 }
-# Algorithmic bytes per fluid particle of the streaming kernels (unique state
-# read and written), per cell for the scan, per active wall for the wall
-# pressure
-BYTES_PER_PARTICLE = {"predict": 100, "scatter": 28, "gather": 212, "neighbors": 400, "continuity": 500,
-                      "momentum": 500}
+# Algorithmic bytes of one launch (the unique data it must read and write
+# once): per fluid particle for the streaming kernels, per cell for the scan,
+# and for the neighbour build its state (position, cell, row mask, counts: 50
+# bytes per particle) plus 4 bytes per list entry and per tagged wall
+BYTES_PER_PARTICLE = {"predict": 100, "scatter": 28, "gather": 212}
+NB_BYTES_PER_PARTICLE = 50
+NB_BYTES_PER_ENTRY = 4
 BYTES_PER_CELL_SCAN = 8
 BYTES_PER_ACTIVE_WALL = 48
+# the whole step's algorithmic bytes per fluid particle: state read and
+# written by the three sweeps plus the sort and reorder (no neighbour lists,
+# which are this design's own working data)
+STEP_BYTES_PER_PARTICLE = 300
+# the same step with this design's lists and per-kernel state traffic, for
+# the design-inclusive figure kept beside it
+DESIGN_BYTES_PER_PARTICLE = {"predict": 100, "scatter": 28, "gather": 212, "neighbors": 400,
+                             "continuity": 500, "momentum": 500}
+CANDIDATE_TEST_FLOPS = 11   # r (6) and |r|^2 (5) per 27-cell candidate
 FP32_LANES_PER_SM = 128
-N_SM = 152
+ISSUE_PER_SM_PER_CLOCK = 4  # one warp instruction per scheduler per cycle
 
 
 def parse():
@@ -237,6 +249,98 @@ def measured_peaks():
         return {}
 
 
+def device_peaks():
+    """Roofline denominators: HBM from MEASURED_PEAKS.json (the driver's copy
+    measurement; else the fallback figure), FP32 FMA and instruction issue
+    from the device's SM count and the maximum SM clock."""
+    import torch
+    sm = int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    p = measured_peaks()
+    sm_max = float(p.get("sm_max_mhz", 2070.0))
+    return {"sm_count": sm, "sm_max_mhz": sm_max,
+            "fp32_tflops": sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12,
+            "issue_twips": sm * ISSUE_PER_SM_PER_CLOCK * sm_max * 1e6 / 1e12,
+            "hbm_gbs": float(p.get("hbm_gbs", 6800.0)),
+            "hbm_source": "measured copy (MEASURED_PEAKS.json)" if "hbm_gbs" in p else "fallback 6.8 TB/s"}
+
+
+def kernel_work(kind: str, n_fluid: int, ff: float, fw: float, active: float, n_cells: int):
+    """Algorithmic work of one launch of a step kernel: ("alu", flops) for the
+    pair sweeps, ("hbm", bytes) for the neighbour build and the streaming
+    kernels."""
+    if kind == "momentum":
+        return "alu", ff * FLOPS_PAIR["momentum_ff"] + fw * FLOPS_PAIR["momentum_fw"]
+    if kind == "continuity":
+        return "alu", ff * FLOPS_PAIR["continuity_ff"] + fw * FLOPS_PAIR["continuity_fw"]
+    if kind == "wall_pressure":
+        return "alu", fw * FLOPS_PAIR["wall_pressure"]
+    if kind == "neighbors":
+        return "hbm", n_fluid * NB_BYTES_PER_PARTICLE + NB_BYTES_PER_ENTRY * (ff + fw + active)
+    if kind == "scan":
+        return "hbm", n_cells * BYTES_PER_CELL_SCAN
+    return "hbm", n_fluid * BYTES_PER_PARTICLE[kind]
+
+
+def kernel_roofline(kind: str, ms: float, work, peaks: dict) -> dict:
+    """achieved = algorithmic work per launch / launch time, against the FP32
+    FMA peak (pair sweeps) or the measured copy bandwidth (the rest)."""
+    bound, amount = work
+    if bound == "alu":
+        ach = amount / (ms / 1e3) / 1e12
+        r = {"bound": "alu", "kernel": f"k_{kind}", "achieved": ach, "peak": peaks["fp32_tflops"],
+             "unit": "TFLOP/s", "frac": ach / peaks["fp32_tflops"], "flops_per_launch": amount,
+             "peak_source": f"FP32 FMA: {peaks['sm_count']} SMs (device property) x {FP32_LANES_PER_SM} "
+                            f"lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz (derived)"}
+    else:
+        ach = amount / (ms / 1e3) / 1e9
+        r = {"bound": "hbm", "kernel": f"k_{kind}", "achieved": ach, "peak": peaks["hbm_gbs"],
+             "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "bytes_per_launch": amount,
+             "peak_source": peaks["hbm_source"]}
+    r["traffic"] = ncu_traffic(f"k_{kind}")
+    r["ms_per_launch"] = ms
+    # the same launch against the SMs' instruction issue rate, from ncu's
+    # warp-instruction count of the committed capture (current sources only)
+    inst = ncu_traffic(f"k_{kind}", "warp_inst_per_launch")
+    if inst:
+        issue = inst / (ms / 1e3) / 1e12
+        r["issue"] = {"achieved": issue, "peak": peaks["issue_twips"], "unit": "T warp-instructions/s",
+                      "frac": issue / peaks["issue_twips"], "warp_inst_per_launch": inst,
+                      "source": "smsp__inst_executed.sum of the committed ncu capture"}
+    return r
+
+
+def step_roofline(n_fluid: int, ff: float, fw: float, t_step_us: float, peaks: dict) -> dict:
+    """The whole step's algorithmic work (the pair formulas of continuity,
+    momentum and wall pressure; the state bytes of the sweeps, sort and
+    reorder) as a lower bound on its time, max(flops / FP32 peak, bytes / HBM
+    peak), over the measured step time."""
+    flops = (ff * (FLOPS_PAIR["continuity_ff"] + FLOPS_PAIR["momentum_ff"])
+             + fw * (FLOPS_PAIR["continuity_fw"] + FLOPS_PAIR["momentum_fw"] + FLOPS_PAIR["wall_pressure"]))
+    nbytes = STEP_BYTES_PER_PARTICLE * n_fluid
+    t_f = flops / (peaks["fp32_tflops"] * 1e12) * 1e6
+    t_b = nbytes / (peaks["hbm_gbs"] * 1e9) * 1e6
+    return {"flops": flops, "bytes": nbytes, "flops_per_particle": flops / n_fluid,
+            "us_at_fp32_peak": t_f, "us_at_hbm_peak": t_b, "us_measured": t_step_us,
+            "bound": "alu" if t_f >= t_b else "hbm", "frac": max(t_f, t_b) / t_step_us,
+            "peaks": f"FP32 {peaks['fp32_tflops']:.1f} TFLOP/s (derived), HBM {peaks['hbm_gbs']:.0f} GB/s "
+                     f"({peaks['hbm_source']})"}
+
+
+def step_roofline_design(n_fluid: int, ff: float, fw: float, active: float, n_cells: int, cand: int,
+                         t_step_us: float, peaks: dict) -> dict:
+    """The same bound with this design's own work added: the 27-cell
+    candidate tests and the neighbour lists' bytes."""
+    flops = (cand * CANDIDATE_TEST_FLOPS
+             + ff * (FLOPS_PAIR["continuity_ff"] + FLOPS_PAIR["momentum_ff"])
+             + fw * (FLOPS_PAIR["continuity_fw"] + FLOPS_PAIR["momentum_fw"] + FLOPS_PAIR["wall_pressure"]))
+    nbytes = (n_fluid * sum(DESIGN_BYTES_PER_PARTICLE.values()) + n_cells * BYTES_PER_CELL_SCAN
+              + active * BYTES_PER_ACTIVE_WALL)
+    t_f = flops / (peaks["fp32_tflops"] * 1e12) * 1e6
+    t_b = nbytes / (peaks["hbm_gbs"] * 1e9) * 1e6
+    return {"flops": flops, "bytes": nbytes, "candidate_tests": cand, "us_at_fp32_peak": t_f,
+            "us_at_hbm_peak": t_b, "us_measured": t_step_us, "frac": max(t_f, t_b) / t_step_us}
+
+
 # --------------------------------------------------------------- CPU oracle
 def cpu_baseline(sc, active_walls: float, seconds: float):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample of
@@ -350,8 +454,7 @@ def run_gpu(args):
     shares = {k: round(warm[k]["ms"] / warm_total, 4) for k in step_kinds if warm_total > 0}
     kernel_us = {k: round(warm[k]["ms"] * 1e3 / max(args.warmup, 1), 2) for k in step_kinds}
 
-    st0 = sim.state()
-    ff, fw, active0 = pair_counts(st0["x"], sc.wall_pos, sc.h)
+    ff0, fw0 = sim.neighbor_totals()
     steps0, act_steps0 = sim.counters()
     launches0 = sum(v["launches"] for v in sim.profile_read().values())
 
@@ -382,8 +485,7 @@ def run_gpu(args):
     steps1, act_steps1 = sim.counters()
     launches1 = sum(v["launches"] for v in prof.values())
     active_mean = (act_steps1 - act_steps0) / max(steps1 - steps0, 1)
-    st1 = sim.state()
-    ff1, fw1, active1 = pair_counts(st1["x"], sc.wall_pos, sc.h)
+    ff1, fw1 = sim.neighbor_totals()
     cand_tests = candidate_tests(sim)
     # the dominant kernel's launch duration, CUDA events around each launch,
     # on the steps that follow the timed region (same workload, cold L2)
@@ -402,60 +504,19 @@ def run_gpu(args):
     value, t_ms = replica_throughput(pg, t_ms, parts * args.steps, "cuda")
     value_fluid, _ = replica_throughput(pg, t_ms, float(sc.n_fluid * args.steps), "cuda")
 
-    # roofline of the dominant kernel (FP32 ALU bound: no dense contraction)
-    pairs_ff = 0.5 * (ff + ff1)
-    pairs_fw = 0.5 * (fw + fw1)
-    if dominant == "momentum":
-        flops = pairs_ff * FLOPS_PAIR["momentum_ff"] + pairs_fw * FLOPS_PAIR["momentum_fw"]
-    elif dominant == "continuity":
-        flops = pairs_ff * FLOPS_PAIR["continuity_ff"] + pairs_fw * FLOPS_PAIR["continuity_fw"]
-    elif dominant == "wall_pressure":
-        flops = pairs_fw * FLOPS_PAIR["wall_pressure"]
-    elif dominant == "neighbors":
-        flops = cand_tests * FLOPS_PAIR["neighbors"]
-    else:
-        flops = None
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    roofline = None
-    if flops:
-        ach = flops / (dom_ms / 1e3) / 1e12
-        roofline = {"bound": "alu", "kernel": f"k_{dominant}", "achieved": ach, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": ach / fp32_peak,
-                    "traffic": ncu_traffic(f"k_{dominant}"),
-                    "peak_source": f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x "
-                                   f"{sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS.json)",
-                    "flops_per_launch": flops, "ms_per_launch": dom_ms}
-        # the same launch against the SMs' instruction issue rate (4 schedulers
-        # per SM, one warp instruction per cycle each): the bound of an
-        # issue-limited kernel, from ncu's instruction count of the capture
-        inst = ncu_traffic(f"k_{dominant}", "warp_inst_per_launch")
-        if inst:
-            issue_peak = N_SM * 4 * sm_max * 1e6 / 1e12
-            issue = inst / (dom_ms / 1e3) / 1e12
-            roofline["issue"] = {"achieved": issue, "peak": issue_peak, "unit": "T warp-instructions/s",
-                                 "frac": issue / issue_peak,
-                                 "warp_inst_per_launch": inst,
-                                 "source": "smsp__inst_executed.sum of the committed ncu capture"}
-
-    # the whole step against both roofs: its algorithmic flops and bytes give
-    # a lower bound on its time, max(flops / FP32 peak, bytes / HBM peak)
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    step_flops = (cand_tests * FLOPS_PAIR["neighbors"]
-                  + pairs_ff * (FLOPS_PAIR["continuity_ff"] + FLOPS_PAIR["momentum_ff"])
-                  + pairs_fw * (FLOPS_PAIR["continuity_fw"] + FLOPS_PAIR["momentum_fw"]
-                                + FLOPS_PAIR["wall_pressure"]))
-    step_bytes = (sc.n_fluid * sum(BYTES_PER_PARTICLE.values()) + n_cells * BYTES_PER_CELL_SCAN
-                  + active_mean * BYTES_PER_ACTIVE_WALL)
-    t_flops = step_flops / (fp32_peak * 1e12) * 1e6
-    t_bytes = step_bytes / (hbm * 1e9) * 1e6
+    # roofline of the dominant kernel: the pair sweeps against the FP32 FMA
+    # peak (no dense contraction), the neighbour build and the streaming
+    # kernels against the measured copy bandwidth
+    pairs_ff = 0.5 * (ff0 + ff1)
+    pairs_fw = 0.5 * (fw0 + fw1)
+    peaks = device_peaks()
+    roofline = kernel_roofline(dominant, dom_ms,
+                               kernel_work(dominant, sc.n_fluid, pairs_ff, pairs_fw, active_mean, n_cells), peaks)
     t_step = t_ms / args.steps * 1e3
-    step_roof = {"flops": step_flops, "bytes": step_bytes, "us_at_fp32_peak": t_flops,
-                 "us_at_hbm_peak": t_bytes, "us_measured": t_step,
-                 "frac": max(t_flops, t_bytes) / t_step,
-                 "peaks": f"FP32 {fp32_peak:.1f} TFLOP/s (derived), HBM {hbm:.0f} GB/s (measured copy)"}
-    streaming = streaming_roofline(kernel_us, sc.n_fluid, n_cells, hbm)
+    step_roof = step_roofline(sc.n_fluid, pairs_ff, pairs_fw, t_step, peaks)
+    step_roof_design = step_roofline_design(sc.n_fluid, pairs_ff, pairs_fw, active_mean, n_cells, cand_tests,
+                                            t_step, peaks)
+    streaming = streaming_roofline(kernel_us, sc.n_fluid, n_cells, peaks["hbm_gbs"])
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -467,7 +528,9 @@ def run_gpu(args):
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "kernel_share_warmup": shares, "kernel_us_per_step_warmup": kernel_us,
                        "step_launch": "one CUDA graph per step"},
-            "roofline": roofline, "step_roofline": step_roof, "streaming_roofline": streaming,
+            "roofline": roofline, "step_roofline": step_roof, "step_roofline_design": step_roof_design,
+            "streaming_roofline": streaming,
+            "pairs_per_fluid_particle": {"fluid": pairs_ff / sc.n_fluid, "wall": pairs_fw / sc.n_fluid},
             "gpu_launches": int(launches1 - launches0), "clocks": clk,
             "host_wall_s": wall1 - wall0}
 
@@ -542,7 +605,8 @@ def accuracy(sc, nsteps: int = 20):
     def rel(a, b, floor=0.0):
         return float(np.abs(a - b).max() / max(np.abs(b).max(), floor))
 
-    out = {"steps": nsteps, "dt": dt, "against": "FP64 oracle (C, host)"}
+    out = {"steps": nsteps, "dt": dt, "against": "FP64 oracle (C, host)",
+           "norm": "max over particles of |gpu - oracle| / max |oracle| per field (a: / max(max|a|, |g|))"}
     for name, prec in (("fp32", sph.SPH_FP32), ("fp64_plain", sph.SPH_FP64_PLAIN)):
         s = sph.Simulation(sc, precision=prec)
         s.step(nsteps, dt)
@@ -553,6 +617,10 @@ def accuracy(sc, nsteps: int = 20):
                      "pw_rel_err": rel(g["pw"], ow["pw"]),
                      "a_rel_err": rel(g["a"], o["a"], gnorm),
                      "drho_dt_rel_err": rel(g["drho_dt"], o["drho_dt"])}
+        if len(sc.phases) > 1:  # per phase: a light phase has its own FP32 floor
+            out[name]["a_rel_err_by_phase"] = [
+                rel(g["a"][sc.fluid_phase == k], o["a"][sc.fluid_phase == k], gnorm)
+                for k in range(len(sc.phases))]
     return out
 
 
@@ -628,12 +696,31 @@ def adjoint_block(stream, reps: int = 3):
             "fp32_vs_fp64_param_grad": {k: [g32[k], g64[k]] for k in ("c0", "gamma_p", "mu")}}
 
 
-def other_workloads(stream, flush, steps: int = 50):
-    """FP32 throughput of the two larger configurations (same step, same
-    timing method, fewer steps): the two-phase ramp/cylinder tank and the
-    10.35 M-particle dam break."""
+def timed_steps(sim, steps: int, stream, flush) -> float:
+    """Milliseconds of `steps` enqueued steps, CUDA events around each on the
+    library's stream, a 256 MB write before each (cold L2)."""
     import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        sim.step_async(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    sim.sync()
+    return float(sum(a.elapsed_time(b) for a, b in ev))
+
+
+def other_workloads(stream, flush, steps: int = 50, fp64_steps: int = 20):
+    """The two larger configurations, each as a line of its own: the
+    two-phase ramp/cylinder tank and the 10.35 M-particle dam break.  FP32
+    throughput (same step, same timing method, fewer steps), the per-kernel
+    split, the dominant kernel's roofline and the step's; the plain FP64 form's
+    throughput on the same workload; both forms' error against the FP64 oracle
+    after one step of fixed dt from the created state."""
     from paper_2110_02621_gb300 import scenes, sph
+    peaks = device_peaks()
     out = {}
     for name in ("two_phase_ramp_cylinder", "dam_break_10m"):
         try:
@@ -643,33 +730,48 @@ def other_workloads(stream, flush, steps: int = 50):
                 flush.zero_()
                 sim.step(1)
             s0, a0 = sim.counters()
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                  for _ in range(steps)]
-            for k in range(steps):
-                flush.zero_()
-                ev[k][0].record(stream)
-                sim.step_async(1)
-                ev[k][1].record(stream)
-            torch.cuda.synchronize()
-            sim.sync()
-            t_ms = sum(a.elapsed_time(b) for a, b in ev)
+            ff0, fw0 = sim.neighbor_totals()
+            t_ms = timed_steps(sim, steps, stream, flush)
             s1, a1 = sim.counters()
+            ff1, fw1 = sim.neighbor_totals()
             sim.profile(sph.KERNEL_KINDS)
-            sim.step(3)
+            for _ in range(3):
+                flush.zero_()
+                sim.step(1)
             prof = sim.profile_read()
             _, n_cells, _ = sim.grid()
             sim.close()
             active = (a1 - a0) / max(s1 - s0, 1)
+            ff, fw = 0.5 * (ff0 + ff1), 0.5 * (fw0 + fw1)
             kus = {k: round(v["ms"] * 1e3 / 3, 1) for k, v in prof.items() if v["timed"]}
+            dom = max((k for k in kus if k != "other"), key=lambda k: kus[k])
+            t_step = t_ms / steps * 1e3
+            sim64 = sph.Simulation(sc, precision=sph.SPH_FP64_PLAIN, stream=stream.cuda_stream)
+            for _ in range(2):
+                flush.zero_()
+                sim64.step(1)
+            s64, a64 = sim64.counters()
+            t64 = timed_steps(sim64, fp64_steps, stream, flush)
+            s64b, a64b = sim64.counters()
+            sim64.close()
+            act64 = (a64b - a64) / max(s64b - s64, 1)
             out[name] = {"n_fluid": sc.n_fluid, "n_wall": sc.n_wall, "active_wall_mean": round(active, 1),
                          "ms_per_step": t_ms / steps, "steps": steps,
                          "value": (sc.n_fluid + active) * steps / (t_ms / 1e3) / 1e6,
                          "value_fluid_only": sc.n_fluid * steps / (t_ms / 1e3) / 1e6, "unit": UNIT,
-                         "kernel_us_per_step": kus,
-                         "streaming_roofline": streaming_roofline(
-                             kus, sc.n_fluid, n_cells, float(measured_peaks().get("hbm_gbs", 6800.0)))}
+                         "dtype": "f32", "kernel_us_per_step": kus,
+                         "pairs_per_fluid_particle": {"fluid": ff / sc.n_fluid, "wall": fw / sc.n_fluid},
+                         "roofline": kernel_roofline(dom, kus[dom] / 1e3,
+                                                     kernel_work(dom, sc.n_fluid, ff, fw, active, n_cells), peaks),
+                         "step_roofline": step_roofline(sc.n_fluid, ff, fw, t_step, peaks),
+                         "streaming_roofline": streaming_roofline(kus, sc.n_fluid, n_cells, peaks["hbm_gbs"]),
+                         "fp64_plain": {"ms_per_step": t64 / fp64_steps, "steps": fp64_steps, "dtype": "f64",
+                                        "value": (sc.n_fluid + act64) * fp64_steps / (t64 / 1e3) / 1e6,
+                                        "value_fluid_only": sc.n_fluid * fp64_steps / (t64 / 1e3) / 1e6,
+                                        "fp32_speedup": (t64 / fp64_steps) / (t_ms / steps)}}
+            out[name]["accuracy"] = accuracy(sc, 1)
         except Exception as e:  # reported, not fatal: the main line stands on its own
-            out[name] = {"error": f"{type(e).__name__}: {e}"}
+            out.setdefault(name, {})["error"] = f"{type(e).__name__}: {e}"
     return out
 
 

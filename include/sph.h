@@ -206,6 +206,34 @@ sph_status sph_get_cells(sph_ctx* ctx, uint32_t* key_fluid, int32_t* order_fluid
                          int32_t* start_fluid, uint32_t* key_wall,
                          int32_t* order_wall, int32_t* start_wall);
 
+/* The neighbour sets of the last neighbour build (Sec. 3: the particles
+ * within the support 2h of each fluid particle, found through the 27 cells
+ * around its own), as the continuity and momentum sweeps of the last step
+ * visited them: for fluid particle i (original id), the original ids of the
+ * fluid particles j with 0 < |r_ij| < 2h and of the wall particles w with
+ * 0 < |r_iw| < 2h, where |r|^2 is evaluated in the context's precision from
+ * the cell-relative positions (the sweeps' own test).  A particle whose
+ * list overflowed the fixed list capacity is reported with the set its
+ * sweeps scanned from the cells instead.  Particles outside the grid have
+ * none.  Host arrays:
+ *   fluid_offsets[n_fluid + 1], wall_offsets[n_fluid + 1] (int64): the
+ *     neighbours of i are fluid_ids[fluid_offsets[i] .. fluid_offsets[i+1])
+ *     and wall_ids[wall_offsets[i] .. wall_offsets[i+1]), ascending;
+ *   fluid_ids[fluid_cap], wall_ids[wall_cap] (int32);
+ *   overflow[2]: the number of fluid particles whose fluid / wall list
+ *     overflowed (and were scanned).
+ * Any pointer may be NULL.  Call once with NULL id arrays to learn the
+ * totals (fluid_offsets[n_fluid], wall_offsets[n_fluid]); a capacity below
+ * the total gives SPH_ERR_ARG with the offsets written.  When the lists no
+ * longer hold the build of the current state (after sph_tape kept them with
+ * its products, or after sph_backward), the builder runs again on the
+ * current state, which reproduces them.  An inspection call, not part of
+ * the step: it allocates device memory on the stream and synchronises.
+ * Errors: SPH_ERR_ARG, SPH_ERR_CUDA, SPH_ERR_STATE. */
+sph_status sph_get_neighbors(sph_ctx* ctx, int64_t* fluid_offsets, int32_t* fluid_ids,
+                             int64_t fluid_cap, int64_t* wall_offsets, int32_t* wall_ids,
+                             int64_t wall_cap, int64_t overflow[2]);
+
 /* FP64 device reductions of the fluid state: out[8] = {total mass,
  * momentum x, y, z, kinetic energy, potential energy -sum m g.r, U_max,
  * number of particles outside the grid}.  Synchronises. */
@@ -398,7 +426,14 @@ void sph_destroy(sph_ctx* ctx);
  * dims[3] cells, the particle order sorted by (key, id) and the first
  * sorted slot of each cell.  Outputs are device arrays: key[n] (per id),
  * order[n], start[n_cells + 1] with n_cells = dims[0]*dims[1]*dims[2].
+ * Particles outside the grid get key 0xFFFFFFFF and come last in order.
  * Scratch memory is allocated and freed on the stream inside the call.
+ * Limits: every extent >= 1 and n_cells <= 2^24 - 2 (checked factor by
+ * factor, before any launch: SPH_ERR_ARG); n <= 2e9.  Cost: each particle
+ * finds its rank inside its cell by counting the smaller ids of that cell,
+ * so a cell holding k particles costs k^2 reads.  This suits SPH grids
+ * (cells of side 2h hold about 20 particles) but not coarse grids over
+ * clustered points: a cell of 10^5 points costs 10^10 reads.
  * Errors: SPH_ERR_ARG, SPH_ERR_OOM, SPH_ERR_CUDA. */
 sph_status sph_bin_sort(const double* pos, int64_t n, const double lo[3],
                         double h, const int32_t dims[3], uint32_t* key,

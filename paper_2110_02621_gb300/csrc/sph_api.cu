@@ -185,6 +185,19 @@ sph_status sph_get_cells(sph_ctx* ctx, uint32_t* key_fluid, int32_t* order_fluid
                                                  start_wall);
 }
 
+sph_status sph_get_neighbors(sph_ctx* ctx, int64_t* fluid_offsets, int32_t* fluid_ids, int64_t fluid_cap,
+                             int64_t* wall_offsets, int32_t* wall_ids, int64_t wall_cap, int64_t overflow[2])
+{
+    sph_status s = usable(ctx);
+    if (s != SPH_OK) return s;
+    if (fluid_cap < 0 || wall_cap < 0) {
+        ctx->sim->err = "capacities must be >= 0";
+        return SPH_ERR_ARG;
+    }
+    return ctx->sim->get_neighbors(fluid_offsets, fluid_ids, fluid_cap, wall_offsets, wall_ids, wall_cap,
+                                   overflow);
+}
+
 sph_status sph_diagnostics(sph_ctx* ctx, double out[8])
 {
     sph_status s = usable(ctx);
@@ -340,12 +353,8 @@ sph_status sph_bin_sort(const double* pos, int64_t n, const double lo[3], double
 {
     if (n < 0 || n > 2000000000 || !lo || !dims || !(h > 0) || !start || (n > 0 && (!pos || !key || !order)))
         return SPH_ERR_ARG;
-    int64_t n_cells = 1;
-    for (int d = 0; d < 3; ++d) {
-        if (dims[d] < 1) return SPH_ERR_ARG;
-        n_cells *= dims[d];
-    }
-    if (n_cells > sph::scan_max_len() - 2) return SPH_ERR_ARG;
+    const int64_t n_cells = sph::grid_cell_count(dims);
+    if (n_cells < 0) return SPH_ERR_ARG;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     sph::BinSortScratch L = sph::bin_sort_scratch_layout(n, n_cells);
     char* scratch = nullptr;

@@ -3,6 +3,7 @@
 // Included once per precision (sim_f32.cu, sim_f64.cu).
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -734,6 +735,127 @@ class Sim final : public SimBase {
         return SPH_OK;
     }
 
+    // The neighbour sets the last sweeps visited (sph_get_neighbors), in
+    // original ids, each particle's ids ascending.  When the context's lists
+    // do not hold the build of the current state (after a taped step that
+    // wrote its lists elsewhere, or a backward sweep), the builder runs again
+    // on the current state first: it is deterministic, so the lists are
+    // those of the last step.
+    sph_status get_neighbors(int64_t* f_off, int32_t* f_ids, int64_t f_cap, int64_t* w_off, int32_t* w_ids,
+                             int64_t w_cap, int64_t overflow[2])
+    {
+        const size_t lanes = (size_t)LP * (size_t)nf_;
+        if (nf_ == 0) {
+            if (f_off) f_off[0] = 0;
+            if (w_off) w_off[0] = 0;
+            if (overflow) overflow[0] = overflow[1] = 0;
+            return SPH_OK;
+        }
+        if (!lists_current_) {
+            sph_status s = neighbors(pos_[0], cell_[par_]);
+            if (s != SPH_OK) return s;
+        }
+        int32_t* lc = nullptr;
+        unsigned long long* dof = nullptr;
+        SPH_CUDA(cudaMallocAsync(&lc, sizeof(int32_t) * 2 * lanes, stream));
+        SPH_CUDA(cudaMallocAsync(&dof, sizeof(unsigned long long) * 2, stream));
+        SPH_CUDA(cudaMemsetAsync(dof, 0, sizeof(unsigned long long) * 2, stream));
+        const unsigned nb = (unsigned)((lanes + LBLOCK - 1) / LBLOCK);
+        if (P_.periodic)
+            k_nb_count<T, true><<<nb, LBLOCK, 0, stream>>>(C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0],
+                                                           wpos_, cell_[par_], lc, dof);
+        else
+            k_nb_count<T, false><<<nb, LBLOCK, 0, stream>>>(C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0],
+                                                            wpos_, cell_[par_], lc, dof);
+        SPH_LAUNCH();
+        std::vector<int32_t> hc(2 * lanes), hid((size_t)nf_);
+        unsigned long long hof[2] = {0, 0};
+        SPH_CUDA(cudaMemcpyAsync(hc.data(), lc, sizeof(int32_t) * 2 * lanes, cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaMemcpyAsync(hof, dof, sizeof hof, cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaMemcpyAsync(hid.data(), id_[par_], sizeof(int32_t) * (size_t)nf_, cudaMemcpyDeviceToHost,
+                                 stream));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        SPH_CUDA(cudaFreeAsync(lc, stream));
+        SPH_CUDA(cudaFreeAsync(dof, stream));
+        if (overflow) {
+            overflow[0] = (int64_t)hof[0];
+            overflow[1] = (int64_t)hof[1];
+        }
+        // lane offsets in sorted order (fluid lanes, then wall lanes), and
+        // per-particle counts in original order
+        std::vector<int64_t> loff(2 * lanes + 2);
+        std::vector<int64_t> cf((size_t)nf_ + 1, 0), cw((size_t)nf_ + 1, 0);
+        int64_t tf = 0, tw = 0;
+        for (size_t t = 0; t < lanes; ++t) {
+            loff[t] = tf;
+            tf += hc[t];
+            cf[(size_t)hid[t / LP]] += hc[t];
+        }
+        for (size_t t = 0; t < lanes; ++t) {
+            loff[lanes + t] = tw;
+            tw += hc[lanes + t];
+            cw[(size_t)hid[t / LP]] += hc[lanes + t];
+        }
+        auto to_offsets = [&](std::vector<int64_t>& c, int64_t* out) {
+            int64_t acc = 0;
+            for (size_t i = 0; i <= (size_t)nf_; ++i) {
+                const int64_t v = i < (size_t)nf_ ? c[i] : 0;
+                c[i] = acc;
+                acc += v;
+            }
+            if (out) memcpy(out, c.data(), sizeof(int64_t) * ((size_t)nf_ + 1));
+        };
+        to_offsets(cf, f_off);
+        to_offsets(cw, w_off);
+        if ((f_ids && f_cap < tf) || (w_ids && w_cap < tw)) {
+            char buf[160];
+            snprintf(buf, sizeof buf, "id buffers too small: %lld fluid and %lld wall entries needed",
+                     (long long)tf, (long long)tw);
+            err = buf;
+            return SPH_ERR_ARG;
+        }
+        if (!f_ids && !w_ids) return SPH_OK;
+        int64_t* doff = nullptr;
+        int32_t *dout_f = nullptr, *dout_w = nullptr;
+        SPH_CUDA(cudaMallocAsync(&doff, sizeof(int64_t) * 2 * lanes, stream));
+        SPH_CUDA(cudaMallocAsync(&dout_f, sizeof(int32_t) * (size_t)(tf > 0 ? tf : 1), stream));
+        SPH_CUDA(cudaMallocAsync(&dout_w, sizeof(int32_t) * (size_t)(tw > 0 ? tw : 1), stream));
+        SPH_CUDA(cudaMemcpyAsync(doff, loff.data(), sizeof(int64_t) * 2 * lanes, cudaMemcpyHostToDevice, stream));
+        if (P_.periodic)
+            k_nb_fill<T, true><<<nb, LBLOCK, 0, stream>>>(C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0],
+                                                          wpos_, cell_[par_], id_[par_], wid_, doff, dout_f, dout_w);
+        else
+            k_nb_fill<T, false><<<nb, LBLOCK, 0, stream>>>(C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0],
+                                                           wpos_, cell_[par_], id_[par_], wid_, doff, dout_f,
+                                                           dout_w);
+        SPH_LAUNCH();
+        std::vector<int32_t> hf((size_t)tf), hw((size_t)tw);
+        if (tf > 0)
+            SPH_CUDA(cudaMemcpyAsync(hf.data(), dout_f, sizeof(int32_t) * (size_t)tf, cudaMemcpyDeviceToHost, stream));
+        if (tw > 0)
+            SPH_CUDA(cudaMemcpyAsync(hw.data(), dout_w, sizeof(int32_t) * (size_t)tw, cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        SPH_CUDA(cudaFreeAsync(doff, stream));
+        SPH_CUDA(cudaFreeAsync(dout_f, stream));
+        SPH_CUDA(cudaFreeAsync(dout_w, stream));
+        // each particle's lanes are consecutive: move its entries to its
+        // original id's range and sort them
+        auto place = [&](const std::vector<int32_t>& src, const std::vector<int64_t>& start, size_t base,
+                         int32_t* out) {
+            for (size_t i = 0; i < (size_t)nf_; ++i) {
+                const int64_t b = loff[base + LP * i];
+                const int64_t e = i + 1 < (size_t)nf_ ? loff[base + LP * (i + 1)] : (base ? tw : tf);
+                int32_t* dst = out + start[(size_t)hid[i]];
+                std::copy(src.begin() + b, src.begin() + e, dst);
+                std::sort(dst, dst + (e - b));
+            }
+        };
+        if (f_ids) place(hf, cf, 0, f_ids);
+        if (w_ids) place(hw, cw, lanes, w_ids);
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        return SPH_OK;
+    }
+
     sph_status get_cells(uint32_t* kf, int32_t* of, int32_t* sf, uint32_t* kw, int32_t* ow,
                          int32_t* sw) override
     {
@@ -926,6 +1048,7 @@ class Sim final : public SimBase {
         if ((s = alloc(nbf_, (size_t)SUBF * LP * nf)) != SPH_OK) return s;
         if ((s = alloc(nbw_, (size_t)SUBW * LP * nf)) != SPH_OK) return s;
         if ((s = alloc(ncnt_, (size_t)LP * nf)) != SPH_OK) return s;
+        nbf_live_ = nbf_;
         if ((s = alloc(wtag_, nw)) != SPH_OK) return s;
         if ((s = alloc(d_tag_, 1)) != SPH_OK) return s;
         if ((s = alloc(newcell_, nmax)) != SPH_OK) return s;
@@ -960,6 +1083,7 @@ class Sim final : public SimBase {
     // neighbour lists of the sorted fluid at positions pts / cells cell
     sph_status neighbors(const V4<T>* pts, const int4* cell)
     {
+        lists_current_ = nbf_ == nbf_live_;
         if (nf_ == 0) return SPH_OK;
         {
             // the periodic form only where an axis wraps: the others compile its code out
@@ -1308,6 +1432,7 @@ class Sim final : public SimBase {
 
     sph_status restore(const Ckpt& c)
     {
+        lists_current_ = false;  // the lists belong to a later state
         sph_status s = copy_ckpt(c, false);
         if (s != SPH_OK) return s;
         par_ = c.par;
@@ -1382,6 +1507,8 @@ class Sim final : public SimBase {
     V4<T>* acc_ = nullptr;
     T* sigma_ = nullptr;  // sigma - sigma^0
     int32_t *nbf_ = nullptr, *nbw_ = nullptr;  // neighbour sub-lists (fluid, wall)
+    int32_t* nbf_live_ = nullptr;  // the context's own list buffer (the tape may swap in others)
+    bool lists_current_ = false;   // the own lists hold the build of the current state
     int32_t* ncnt_ = nullptr;                  // per-lane entry counts
     int32_t *wtag_ = nullptr, *d_tag_ = nullptr;  // wall support tags, current tag
     cudaStream_t cap_stream_ = nullptr;

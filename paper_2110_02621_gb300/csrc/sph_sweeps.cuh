@@ -407,6 +407,65 @@ __device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t,
     }
 }
 
+// ------------------------------------------------- neighbour-set export
+// The neighbour sets the continuity and momentum sweeps visit, for the
+// inspection call sph_get_neighbors: each lane walks its share through
+// for_neighbors, the sweeps' own iterator (its sub-list, or its share of the
+// 27 cells after an overflow).  k_nb_count writes lane t's fluid and wall
+// counts to lc[t] and lc[LP n + t] and counts the particles whose fluid or
+// wall lists overflowed (lane 0 of each particle checks its group);
+// k_nb_fill then writes the neighbours' original ids from the lanes'
+// offsets (an exclusive scan of the counts, in sorted lane order).
+template <class T, bool PER>
+__global__ void __launch_bounds__(LBLOCK) k_nb_count(
+    Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
+    const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw, const int32_t* __restrict__ cnt,
+    const V4<T>* __restrict__ pos, const V4<T>* __restrict__ wpos, const int4* __restrict__ cell,
+    int32_t* __restrict__ lc, unsigned long long* overflow)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / LP;
+    if (i >= n) return;
+    const int4 c = cell[i];
+    int nf = 0, nw = 0;
+    if (c.w >= 0) {
+        const int32_t k = cnt[t];
+        for_neighbors<PER>(C, n, t, pos[i], c, nbf, nbw, k, fstart, wstart, pos, wpos,
+                           [&](int, const V4<T>&, T, T, T, T) { ++nf; },
+                           [&](int, const V4<T>&, T, T, T, T) { ++nw; });
+        if (t % LP == 0) {
+            bool of = false, ow = false;
+            for (int l = 0; l < LP; ++l) {
+                of |= (cnt[t + l] & 0xffff) > SUBF;
+                ow |= (cnt[t + l] >> 16) > SUBW;
+            }
+            if (of) atomicAdd(overflow, 1ull);
+            if (ow) atomicAdd(overflow + 1, 1ull);
+        }
+    }
+    lc[t] = nf;
+    lc[(size_t)LP * n + t] = nw;
+}
+
+template <class T, bool PER>
+__global__ void __launch_bounds__(LBLOCK) k_nb_fill(
+    Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
+    const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw, const int32_t* __restrict__ cnt,
+    const V4<T>* __restrict__ pos, const V4<T>* __restrict__ wpos, const int4* __restrict__ cell,
+    const int32_t* __restrict__ id, const int32_t* __restrict__ wid, const int64_t* __restrict__ off,
+    int32_t* __restrict__ out_f, int32_t* __restrict__ out_w)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / LP;
+    if (i >= n) return;
+    const int4 c = cell[i];
+    if (c.w < 0) return;
+    int64_t af = off[t], aw = off[(size_t)LP * n + t];
+    for_neighbors<PER>(C, n, t, pos[i], c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
+                       [&](int j, const V4<T>&, T, T, T, T) { out_f[af++] = id[j]; },
+                       [&](int w, const V4<T>&, T, T, T, T) { out_w[aw++] = wid[w]; });
+}
+
 // ------------------------------------------------------------- continuity
 // Heavy (continuity) phases: Eq. (SPH_star_massConservation) with the
 // Riemann solution of Eq. (RSsolution).  Substituting v* gives, per pair,

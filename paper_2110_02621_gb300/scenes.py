@@ -552,6 +552,38 @@ def perturbed(sc: Scene, jitter: float = 0.3, shift: Tuple[float, float, float] 
         reinit_every=sc.reinit_every if reinit_every is None else reinit_every)
 
 
+def compressed_clump(n: Tuple[int, int, int] = (12, 12, 10), dp: float = 0.01, spacing: float = 0.6,
+                     layers: int = 3, margin: int = 6, vel_scale: float = 0.05, rho_jitter: float = 0.002,
+                     mu: float = 0.0, seed: int = SEED_JITTER) -> Scene:
+    """Fluid compressed to ``spacing`` dp (0.6: about 340 fluid neighbours
+    within 2h = 2.6 dp, against about 80 on the lattice of spacing dp) resting
+    on a floor of ``layers`` wall layers at the same spacing (about 180 wall
+    neighbours for the lowest particles), reaching ``margin`` sites beyond the
+    fluid on every side; the lowest fluid layer sits 0.45 dp above the top wall
+    layer, inside the penalty's reach.  Particle masses stay rho0 dp^3 (the scene's dp), the
+    density starts at rho0 (1 + rho_jitter U(-1, 1)), velocities are random
+    normal of scale ``vel_scale``.  The state an impact compresses to: it
+    makes the per-particle neighbour lists overflow, so the sweeps take their
+    cell-scanning fallback.  No density reinitialisation: the number density is
+    4.6 times the lattice's, which it would turn into a 4.6-fold density."""
+    rng = np.random.default_rng(seed)
+    s = spacing * dp
+    h = 1.3 * dp
+    fluid = lattice(n, s, origin=(0.0, 0.0, -0.25 * s))
+    wall = lattice((n[0] + 2 * margin, n[1] + 2 * margin, layers), s,
+                   origin=(-margin * s, -margin * s, -layers * s))
+    H = n[2] * s
+    lo, hi = _domain(wall, fluid, 2 * h, 2 * h)
+    rho = 1000.0 * (1.0 + rho_jitter * rng.uniform(-1.0, 1.0, fluid.shape[0]))
+    vel = rng.normal(0.0, 1.0, size=fluid.shape) * vel_scale
+    return Scene(
+        name=f"compressed_clump_{n[0]}x{n[1]}x{n[2]}_s{spacing:g}dp", dp=dp, h=h,
+        c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G), lo=lo, hi=hi,
+        phases=[Phase(rho0=1000.0, eos="tait", penalty=True, mu=mu, z_top=H)],
+        fluid_pos=fluid, fluid_vel=vel, fluid_phase=np.zeros(fluid.shape[0], np.int32),
+        wall_pos=wall, reinit_every=0, steps=1, rho_init=rho)
+
+
 def random_points(n: int, box: Tuple[float, float, float], seed: int,
                   dp: float = 0.01) -> np.ndarray:
     """n uniform random points in [0, box) (for neighbour-search checks)."""

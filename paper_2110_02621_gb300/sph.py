@@ -29,7 +29,7 @@ EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_bin_sort_noalloc",
            "sph_profile", "sph_profile_read", "sph_tape", "sph_backward", "sph_step_async",
            "sph_sync", "sph_diagnostics_async", "sph_set_excitation", "sph_time",
-           "sph_probe_pressure", "sph_gauge_height", "sph_tape_budget")
+           "sph_probe_pressure", "sph_gauge_height", "sph_tape_budget", "sph_get_neighbors")
 SPH_GAUGE_MAX_SAMPLES = 65536
 SPH_GAUGE_MAX_LINES = 65535
 SPH_ERR_CAPACITY = 8
@@ -127,6 +127,7 @@ def lib() -> C.CDLL:
         L.sph_probe_pressure.argtypes = [p, p, i32, p, p, i32]
         L.sph_tape_budget.argtypes = [p, i64]
         L.sph_gauge_height.argtypes = [p, p, i32, d, p, i32]
+        L.sph_get_neighbors.argtypes = [p, p, p, i64, p, p, i64, p]
         for name in EXPORTS:
             if name not in ("sph_last_error", "sph_destroy"):
                 getattr(L, name).restype = st
@@ -208,6 +209,11 @@ def sph_grid_info(ctx):
 
 def sph_get_cells(ctx, *arrays):
     return lib().sph_get_cells(ctx, *(_ptr(a) for a in arrays))
+
+
+def sph_get_neighbors(ctx, f_off, f_ids, f_cap: int, w_off, w_ids, w_cap: int, overflow):
+    return lib().sph_get_neighbors(ctx, _ptr(f_off), _ptr(f_ids), int(f_cap), _ptr(w_off), _ptr(w_ids),
+                                   int(w_cap), _ptr(overflow))
 
 
 def sph_diagnostics(ctx, out: np.ndarray):
@@ -403,6 +409,29 @@ class Simulation:
         _check(sph_get_cells(self.ctx, o["key_f"], o["order_f"], o["start_f"], o["key_w"],
                              o["order_w"], o["start_w"]), self.ctx)
         return o
+
+    def neighbors(self) -> dict:
+        """The neighbour sets the last step's sweeps visited (sph_get_neighbors):
+        CSR arrays in original ids, each particle's ids ascending, and the
+        number of particles whose fluid / wall lists overflowed."""
+        n = self.nf
+        f_off, w_off = np.zeros(n + 1, np.int64), np.zeros(n + 1, np.int64)
+        ovf = np.zeros(2, np.int64)
+        _check(sph_get_neighbors(self.ctx, f_off, None, 0, w_off, None, 0, ovf), self.ctx)
+        f_ids = np.zeros(max(int(f_off[-1]), 1), np.int32)
+        w_ids = np.zeros(max(int(w_off[-1]), 1), np.int32)
+        _check(sph_get_neighbors(self.ctx, f_off, f_ids, len(f_ids), w_off, w_ids, len(w_ids), ovf),
+               self.ctx)
+        return {"f_off": f_off, "f_ids": f_ids[:f_off[-1]], "w_off": w_off, "w_ids": w_ids[:w_off[-1]],
+                "overflow": ovf}
+
+    def neighbor_totals(self):
+        """(fluid-fluid, fluid-wall) ordered pair counts of the last build: the
+        totals of sph_get_neighbors, without the ids."""
+        n = self.nf
+        f_off, w_off = np.zeros(n + 1, np.int64), np.zeros(n + 1, np.int64)
+        _check(sph_get_neighbors(self.ctx, f_off, None, 0, w_off, None, 0, None), self.ctx)
+        return int(f_off[-1]), int(w_off[-1])
 
     def diagnostics(self) -> np.ndarray:
         out = np.zeros(8)

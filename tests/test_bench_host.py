@@ -79,3 +79,26 @@ def test_streaming_roofline_arithmetic():
     assert r["gather"]["frac"] == round(gbs / 6800.0, 4)
     assert "momentum" not in r
     assert bench.streaming_roofline({}, 10, 10, 6800.0) == {}
+
+
+def test_roofline_accounting_follows_the_algorithmic_work():
+    """The pair sweeps are bound by FP32 arithmetic and count only the pair
+    formulas; the neighbour build is bound by HBM with its own bytes (state,
+    list entries, wall tags), never by the 27-cell candidate tests; the step's
+    bound uses the pair formulas and 300 state bytes per particle."""
+    import bench
+    peaks = {"sm_count": 152, "sm_max_mhz": 2070.0, "fp32_tflops": 152 * 128 * 2 * 2070e6 / 1e12,
+             "issue_twips": 152 * 4 * 2070e6 / 1e12, "hbm_gbs": 6780.0, "hbm_source": "test"}
+    n, ff, fw, act = 80_400, 80_400 * 78.0, 80_400 * 9.0, 15_000.0
+    kind, flops = bench.kernel_work("momentum", n, ff, fw, act, 60_000)
+    assert kind == "alu" and flops == ff * 50 + fw * 40
+    kind, nbytes = bench.kernel_work("neighbors", n, ff, fw, act, 60_000)
+    assert kind == "hbm" and nbytes == n * 50 + 4 * (ff + fw + act)
+    r = bench.kernel_roofline("neighbors", 0.040, ("hbm", nbytes), peaks)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["frac"] - nbytes / 0.040e-3 / 1e9 / 6780.0) < 1e-12
+    s = bench.step_roofline(n, ff, fw, 150.0, peaks)
+    want_flops = ff * (36 + 50) + fw * (33 + 40 + 24)
+    assert s["flops"] == want_flops and s["bytes"] == 300 * n
+    t = max(want_flops / (peaks["fp32_tflops"] * 1e12), 300 * n / (6780e9)) * 1e6
+    assert abs(s["frac"] - t / 150.0) < 1e-12

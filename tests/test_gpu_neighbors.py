@@ -1,0 +1,250 @@
+"""The integer contract of the neighbour search (Sec. 3: cell binning, sort
+and the particles within 2h) on the GPU, through the C ABI, against the FP64
+oracle: cell keys, sorted order and cell ranges after steps, and the
+neighbour sets the sweeps visit (sph_get_neighbors).
+
+What must agree:
+  * the plain FP64 form: keys, order, ranges and every neighbour set equal
+    the oracle's, bit for bit, after 0, 25 and 100 steps of the benchmark's
+    dam break (80,400 fluid, 120,234 wall particles).  The two evaluate
+    |r|^2 < (2h)^2 in FP64 from cell-relative and from absolute coordinates,
+    so only a pair within a few ulp of the cut-off could differ; after 100
+    steps the trajectories agree to 1e-7 dp, which leaves none in practice;
+  * the FP32 form, against the oracle run on the GPU's own state (its
+    exported positions): every pair whose FP64 |r|^2 lies outside a band of
+    BAND_ULP FP32 ulps around (2h)^2 is in both sets or in neither.  The GPU
+    tests |r|^2 in FP32 from cell offsets rounded to FP32 (and shifts of the
+    FP32 cell side), which moves |r|^2 by at most ~30 ulps of (2h)^2;
+  * the FP32 form, against the oracle's own trajectory: keys equal except
+    for particles closer to a cell face than the positions' disagreement
+    (listed), order and ranges consistent with the keys, and neighbour sets
+    equal except for pairs whose separation is within twice that
+    disagreement of 2h (listed and bounded).
+The compressed clump (fluid and walls at 0.6 dp) overflows the fixed
+per-lane lists: there the sets are those the fallback cell scan visits, and
+one step plus its adjoint must still match the oracle and the reference
+adjoint.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import adjoint as A
+from paper_2110_02621_gb300 import build, scenes as S, sph
+
+pytestmark = pytest.mark.gpu
+
+BAND_ULP = 64  # FP32 ulps of (2h)^2 within which a pair may fall either side
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    oracle.build()
+    sph.lib()
+
+
+def oracle_sets(ref, n):
+    """The oracle's neighbour sets (fluid, wall) of every fluid particle."""
+    f, w = [], []
+    for i in range(n):
+        a, b = ref.neighbors(i)
+        f.append(np.sort(np.asarray(a, np.int64)))
+        w.append(np.sort(np.asarray(b, np.int64)))
+    return f, w
+
+
+def gpu_sets(nb):
+    fo, fi, wo, wi = nb["f_off"], nb["f_ids"], nb["w_off"], nb["w_ids"]
+    n = len(fo) - 1
+    return ([fi[fo[i]:fo[i + 1]].astype(np.int64) for i in range(n)],
+            [wi[wo[i]:wo[i + 1]].astype(np.int64) for i in range(n)])
+
+
+def sym_diff(a, b):
+    """Pairs (i, j) in exactly one of the two families of sets."""
+    out = []
+    for i, (x, y) in enumerate(zip(a, b)):
+        if len(x) == len(y) and np.array_equal(x, y):
+            continue
+        for j in np.setxor1d(x, y):
+            out.append((i, int(j)))
+    return out
+
+
+def check_sets_exact(sim, ref, n):
+    gf, gw = gpu_sets(sim.neighbors())
+    of, ow = oracle_sets(ref, n)
+    assert sym_diff(gf, of) == []
+    assert sym_diff(gw, ow) == []
+    return gf, gw
+
+
+def cells_consistent(g, n_cells):
+    """order is the (key, id) sort of the keys and start the cell ranges."""
+    key = g["key_f"].astype(np.int64)
+    ids = np.arange(len(key))
+    inside = key != 0xFFFFFFFF
+    want = np.lexsort((ids[inside], key[inside]))
+    assert np.array_equal(g["order_f"][:inside.sum()], ids[inside][want])
+    counts = np.bincount(key[inside], minlength=n_cells)
+    assert np.array_equal(g["start_f"], np.concatenate([[0], np.cumsum(counts)]).astype(np.int32))
+
+
+def test_fp64_cells_and_neighbour_sets_bit_exact_after_steps():
+    """Plain FP64 form, the 80k dam break: after create, 25 and 100 CFL steps
+    the step-time binning (keys, order, ranges) and every neighbour set equal
+    the oracle's."""
+    sc = S.dam_break()
+    ref = oracle.OracleSim(sc)
+    with sph.Simulation(sc, precision=sph.SPH_FP64_PLAIN) as sim:
+        for n in (0, 25, 75):
+            if n:
+                sim.step(n)
+                ref.step(n)
+            g, o = sim.cells(), ref.cells()
+            assert np.array_equal(g["key_f"], o["key_f"]), n
+            assert np.array_equal(g["order_f"], o["order_f"].astype(np.int32)), n
+            assert np.array_equal(g["start_f"], o["start_f"].astype(np.int32)), n
+            gf, gw = check_sets_exact(sim, ref, sc.n_fluid)
+            # no fluid list overflows here; the few particles in the tank's
+            # corners that see more wall particles than a wall list holds are
+            # compared above with the sets their sweeps scan
+            assert sim.neighbors()["overflow"][0] == 0
+        # the run moved particles across cells and changed the sets
+        assert np.abs(sim.state()["v"]).max() > 0.1
+        assert sum(len(x) for x in gw) > 0
+
+
+def _pair_r2(xa, xb, pairs):
+    if not pairs:
+        return np.zeros(0)
+    i = np.array([p[0] for p in pairs])
+    j = np.array([p[1] for p in pairs])
+    d = xa[i] - xb[j]
+    return np.einsum("ij,ij->i", d, d)
+
+
+def test_fp32_neighbour_sets_on_the_gpu_state_outside_the_ulp_band():
+    """FP32 form, 80k dam break after 25 and 100 steps: the GPU's sets against
+    the oracle's on the GPU's own positions.  Pairs outside the FP32 ulp band
+    of the cut-off agree exactly; the few inside it are listed and bounded."""
+    sc = S.dam_break()
+    rc2 = (2 * sc.h) ** 2
+    band = BAND_ULP * 2.0 ** -23 * rc2
+    with sph.Simulation(sc) as sim:
+        for n in (25, 75):
+            sim.step(n)
+            st = sim.state()
+            # the oracle on exactly the GPU's state (positions exported in FP64)
+            here = dataclasses.replace(sc, fluid_pos=st["x"], fluid_vel=st["v"], rho_init=st["rho"])
+            ref = oracle.OracleSim(here)
+            gf, gw = gpu_sets(sim.neighbors())
+            of, ow = oracle_sets(ref, sc.n_fluid)
+            df, dw = sym_diff(gf, of), sym_diff(gw, ow)
+            rf = _pair_r2(st["x"], st["x"], df)
+            rw = _pair_r2(st["x"], sc.wall_pos, dw)
+            assert np.all(np.abs(rf - rc2) <= band), [(p, r) for p, r in zip(df, rf) if abs(r - rc2) > band]
+            assert np.all(np.abs(rw - rc2) <= band), [(p, r) for p, r in zip(dw, rw) if abs(r - rc2) > band]
+            total = sum(len(x) for x in of) + sum(len(x) for x in ow)
+            assert len(df) + len(dw) <= 1e-5 * total, (len(df), len(dw), total)
+
+
+def test_fp32_cells_and_sets_against_the_oracle_trajectory():
+    """FP32 form against the FP64 oracle's own run (25 and 100 steps): keys
+    equal except for particles nearer a cell face than twice the largest
+    position disagreement eps (the lattice start puts whole planes of
+    particles on faces); order and ranges are the (key, id) sort of the keys;
+    neighbour sets equal except for pairs whose separation is within 2 eps of
+    2h."""
+    sc = S.dam_break()
+    ref = oracle.OracleSim(sc)
+    cs = 2 * sc.h
+    lo = np.asarray(sc.lo)
+    with sph.Simulation(sc) as sim:
+        for n in (25, 75):
+            sim.step(n)
+            ref.step(n)
+            st, o = sim.state(), ref.fluid()
+            eps = float(np.abs(st["x"] - o["x"]).max())
+            assert eps <= 1e-3 * sc.dp
+            g, oc = sim.cells(), ref.cells()
+            frac = (o["x"] - lo) / cs
+            near_face = (np.abs(frac - np.round(frac)) * cs <= 2 * eps).any(axis=1)
+            diff = g["key_f"] != oc["key_f"]
+            # the lattice puts whole planes of particles on cell faces, where
+            # FP32 and FP64 positions may bin either way: only those may differ
+            assert not np.any(diff & ~near_face), np.nonzero(diff & ~near_face)[0][:10]
+            cells_consistent(g, int(np.prod(g["dims"])))
+            gf, gw = gpu_sets(sim.neighbors())
+            of, ow = oracle_sets(ref, sc.n_fluid)
+            df, dw = sym_diff(gf, of), sym_diff(gw, ow)
+            rf = np.sqrt(_pair_r2(o["x"], o["x"], df))
+            rw = np.sqrt(_pair_r2(o["x"], sc.wall_pos, dw))
+            tol = 2 * eps + BAND_ULP * 2.0 ** -23 * cs
+            assert np.all(np.abs(rf - cs) <= tol) and np.all(np.abs(rw - cs) <= tol), (eps, len(df), len(dw))
+            total = sum(len(x) for x in of) + sum(len(x) for x in ow)
+            assert len(df) + len(dw) <= 1e-4 * total, (len(df), len(dw), total)
+
+
+# ------------------------------------------------------- list overflow
+def test_overflowing_lists_take_the_cell_scan_and_match_the_oracle():
+    """Fluid and walls at 0.6 dp: most particles have more fluid neighbours
+    (up to 340) and many more wall neighbours (up to 131) than the per-lane
+    lists hold, so the sweeps scan the cells instead.  FP64: the visited sets
+    equal the oracle's and one step matches it to rounding; FP32: one step
+    within the single-step tolerances."""
+    sc = S.compressed_clump()
+    dt = 2e-5
+    for prec in (sph.SPH_FP64_PLAIN, sph.SPH_FP32):
+        ref = oracle.OracleSim(sc)
+        with sph.Simulation(sc, precision=prec) as sim:
+            ovf = sim.neighbors()["overflow"]
+            assert ovf[0] > 0.5 * sc.n_fluid and ovf[1] > 100, ovf
+            if prec == sph.SPH_FP64_PLAIN:
+                check_sets_exact(sim, ref, sc.n_fluid)
+            sim.step(1, dt=dt)
+            ref.step(1, dt=dt)
+            if prec == sph.SPH_FP64_PLAIN:
+                check_sets_exact(sim, ref, sc.n_fluid)
+            g, o, ow = sim.state(), ref.fluid(), ref.wall()
+        tol = 1e-9 if prec == sph.SPH_FP64_PLAIN else 2e-5
+        scale = max(np.abs(o["a"]).max(), 9.81)
+        assert np.abs(g["a"] - o["a"]).max() <= tol * scale, np.abs(g["a"] - o["a"]).max() / scale
+        assert np.abs(g["drho_dt"] - o["drho_dt"]).max() <= tol * np.abs(o["drho_dt"]).max()
+        assert np.abs(g["rho"] - o["rho"]).max() <= tol * np.abs(o["rho"]).max()
+        assert np.abs(g["pw"] - ow["pw"]).max() <= 10 * tol * np.abs(ow["pw"]).max()
+        assert np.abs(g["sigma"] - o["sigma"]).max() <= tol * np.abs(o["sigma"]).max()
+        assert np.abs(g["x"] - o["x"]).max() <= (1e-9 if prec == sph.SPH_FP64_PLAIN else 1e-5) * sc.dp
+
+
+def test_overflowing_lists_adjoint_matches_the_reference():
+    """The adjoint kernels walk the same overflowed lists through the same
+    fallback: two taped steps of the compressed clump, gradients of the plain
+    FP64 form within 1e-8 of the reference adjoint, the FP32 form within
+    2e-3."""
+    pytest.importorskip("scipy")
+    sc = S.compressed_clump(mu=0.05)
+    dt = 2e-5
+    ref = oracle.OracleSim(sc)
+    rho0, normals, sigma0 = ref.fluid()["rho"].copy(), ref.wall()["normal"].copy(), ref.sigma0
+    rng = np.random.default_rng(29)
+    seed = {"x": rng.normal(size=(sc.n_fluid, 3)), "v": rng.normal(size=(sc.n_fluid, 3)),
+            "rho": rng.normal(size=sc.n_fluid) * 1e-3, "pw": rng.normal(size=sc.n_wall) * 1e-3}
+    final, o, _ = A.vjp(sc, normals, sigma0, rho0, 2, dt, seed)
+    for prec, tol in ((sph.SPH_FP64_PLAIN, 1e-8), (sph.SPH_FP32, 2e-3)):
+        with sph.Simulation(sc, precision=prec, rho=rho0) as sim:
+            assert sim.neighbors()["overflow"][0] > 0.5 * sc.n_fluid
+            sim.tape(2, dt)
+            g = sim.backward(seed)
+        for k in ("x", "v", "rho"):
+            den = np.abs(o[k]).max()
+            assert np.abs(g[k] - o[k]).max() <= tol * den, (prec, k, np.abs(g[k] - o[k]).max() / den)
+        for k in ("c0", "gamma_p", "mu"):
+            ref_k = float(o[k])
+            assert abs(g[k] - ref_k) <= tol * max(abs(ref_k), 1e-12), (prec, k, g[k], ref_k)
