@@ -12,7 +12,12 @@ Geometry conventions (shared by every generator):
   * wall dummy particles fill ``layers`` lattice layers outside the floor and
     the four side faces, up to the tank height (corners included);
   * the neighbour-grid domain [lo, hi] is the wall bounding box padded by one
-    grid cell (2h) on every side, plus head room above the tank.
+    grid cell (2h) on every side, plus head room above the tank, and its
+    lower corner lies a further dp/10 below: with cells of 2h = 2.6 dp the
+    faces would otherwise pass exactly through lattice sites (every 13th),
+    where the cell of a particle that has barely moved is decided by the last
+    bit of its coordinate; shifted, every site stays at least dp/10 from a
+    face.
 
 Sizes follow the paper's cases (Sec. 4): the smoothing length is h = 1.3 dx
 with support radius 2h, g = 9.81 m/s^2, and the sound speed is chosen as
@@ -115,9 +120,9 @@ def tank_walls(inner: Tuple[int, int], height: int, dp: float,
 
 
 def _domain(wall: np.ndarray, fluid: np.ndarray, cell: float,
-            head_room: float) -> Tuple[tuple, tuple]:
+            head_room: float, dp: float) -> Tuple[tuple, tuple]:
     pts = wall if wall.shape[0] else fluid
-    lo = pts.min(axis=0) - cell
+    lo = pts.min(axis=0) - cell - 0.1 * dp
     hi = pts.max(axis=0) + cell
     hi[2] += head_room
     return tuple(float(v) for v in lo), tuple(float(v) for v in hi)
@@ -137,7 +142,7 @@ def still_water_tank(n_fluid: Tuple[int, int, int] = (20, 20, 20),
     H = nz * dp
     fluid = lattice(n_fluid, dp)
     wall = tank_walls((nx, ny), _count(wall_height, dp), dp, layers)
-    lo, hi = _domain(wall, fluid, 2 * h, 2 * h)
+    lo, hi = _domain(wall, fluid, 2 * h, 2 * h, dp)
     c0 = 10.0 * math.sqrt(G * H)
     return Scene(
         name=f"still_water_tank_{nx}x{ny}x{nz}_dp{dp:g}", dp=dp, h=h, c0=c0,
@@ -168,7 +173,7 @@ def dam_break(tank: Tuple[float, float, float] = (1.6, 0.67, 0.6),
     H = ncz * dp
     fluid = lattice((ncx, ncy, ncz), dp)
     wall = tank_walls((ntx, nty), ntz, dp, layers)
-    lo, hi = _domain(wall, fluid, 2 * h, 0.25 * tank[2])
+    lo, hi = _domain(wall, fluid, 2 * h, 0.25 * tank[2], dp)
     probes = None
     if n_probes > 0:
         side = int(round(math.sqrt(n_probes)))
@@ -234,7 +239,7 @@ def dam_break_obstacle(tank: Tuple[float, float, float] = (3.0, 1.0, 1.6),
         parts.append(lattice((ntx + 2 * layers, nty + 2 * layers, layers), dp,
                              origin=(-layers * dp, -layers * dp, ntz * dp)))
     wall = np.concatenate(parts)
-    lo, hi = _domain(wall, fluid, 2 * h, 0.0 if roof else 0.2)
+    lo, hi = _domain(wall, fluid, 2 * h, 0.0 if roof else 0.2, dp)
     face_x, yc = ox0 * dp, (oy0 + 0.5 * ony) * dp
     top = onz * dp
     sensors = np.array([[face_x, yc, f * top] for f in (0.125, 0.375, 0.625, 0.875)]
@@ -301,7 +306,7 @@ def two_phase_ramp_cylinder(tank: Tuple[float, float, float] = (1.0, 0.5, 0.5),
     box = (np.stack([x[~inside], y[~inside], z[~inside]], axis=1)
            .astype(np.float64) + 0.5) * dp
     wall = np.concatenate([box, obstacle_wall], axis=0)
-    lo, hi = _domain(wall, fluid, 2 * h, 0.0)
+    lo, hi = _domain(wall, fluid, 2 * h, 0.0, dp)
     c0 = 10.0 * math.sqrt(G * H)
     return Scene(
         name=(f"two_phase_ramp_cylinder_{tank[0]:g}x{tank[1]:g}x{tank[2]:g}"
@@ -334,7 +339,7 @@ def two_phase_still_tank(n: Tuple[int, int] = (12, 6), dp: float = 0.01,
     inside = ((x >= 0) & (x < nx) & (y >= 0) & (y < ny) & (z >= 0) & (z < nz))
     wall = (np.stack([x[~inside], y[~inside], z[~inside]], axis=1)
             .astype(np.float64) + 0.5) * dp
-    lo, hi = _domain(wall, fluid, 2 * h, 0.0)
+    lo, hi = _domain(wall, fluid, 2 * h, 0.0, dp)
     return Scene(
         name=f"two_phase_still_tank_{nx}x{ny}x{nz}_dp{dp:g}", dp=dp, h=h,
         c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G), lo=lo, hi=hi,
@@ -455,9 +460,10 @@ def box_walls2d(inner: Tuple[int, int], dp: float, layers: int = 3, roof: bool =
     return pts.astype(np.float64)
 
 
-def _domain2d(wall: np.ndarray, fluid: np.ndarray, cell: float, head: float):
+def _domain2d(wall: np.ndarray, fluid: np.ndarray, cell: float, head: float, dp: float):
     allp = np.concatenate([wall, fluid], axis=0)
-    lo = (float(allp[:, 0].min() - cell), -0.5 * cell, float(allp[:, 2].min() - cell))
+    lo = (float(allp[:, 0].min() - cell - 0.1 * dp), -0.5 * cell,
+          float(allp[:, 2].min() - cell - 0.1 * dp))
     hi = (float(allp[:, 0].max() + cell), 0.5 * cell, float(allp[:, 2].max() + cell + head))
     return lo, hi
 
@@ -475,7 +481,7 @@ def two_phase_hydrostatic_tank_2d(dx: float = 0.01, L: float = 1.0, H: float = 0
     fluid = lattice2d((nx, nz), dx)
     phase = np.where(fluid[:, 2] < H, 0, 1).astype(np.int32)
     wall = box_walls2d((nx, nz), dx, layers, roof=True)
-    lo, hi = _domain2d(wall, fluid, 2 * h, 0.0)
+    lo, hi = _domain2d(wall, fluid, 2 * h, 0.0, dx)
     return Scene(
         name=f"two_phase_hydrostatic_tank_2d_dx{dx:g}", dp=dx, h=h,
         c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G), lo=lo, hi=hi,
@@ -500,7 +506,7 @@ def sloshing_tank_2d(dx: float = 0.01, L: float = 1.3, D: float = 0.9, H: float 
     fluid = lattice2d((nx, nz), dx)
     phase = np.where(fluid[:, 2] < H, 0, 1).astype(np.int32)
     wall = box_walls2d((nx, nz), dx, layers, roof=True)
-    lo, hi = _domain2d(wall, fluid, 2 * h, 0.0)
+    lo, hi = _domain2d(wall, fluid, 2 * h, 0.0, dx)
     return Scene(
         name=f"sloshing_tank_2d_dx{dx:g}", dp=dx, h=h, c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G),
         lo=lo, hi=hi,
@@ -522,7 +528,7 @@ def dam_break_2d(tank: Tuple[float, float] = (0.4, 0.3), column: Tuple[float, fl
     H = ncz * dx
     fluid = lattice2d((ncx, ncz), dx)
     wall = box_walls2d((ntx, ntz), dx, layers, roof=False)
-    lo, hi = _domain2d(wall, fluid, 2 * h, 0.25 * tank[1])
+    lo, hi = _domain2d(wall, fluid, 2 * h, 0.25 * tank[1], dx)
     return Scene(
         name=f"dam_break_2d_{tank[0]:g}x{tank[1]:g}_dx{dx:g}", dp=dx, h=h,
         c0=10.0 * math.sqrt(G * H), g=(0.0, 0.0, -G), lo=lo, hi=hi,
@@ -573,7 +579,7 @@ def compressed_clump(n: Tuple[int, int, int] = (12, 12, 10), dp: float = 0.01, s
     wall = lattice((n[0] + 2 * margin, n[1] + 2 * margin, layers), s,
                    origin=(-margin * s, -margin * s, -layers * s))
     H = n[2] * s
-    lo, hi = _domain(wall, fluid, 2 * h, 2 * h)
+    lo, hi = _domain(wall, fluid, 2 * h, 2 * h, dp)
     rho = 1000.0 * (1.0 + rho_jitter * rng.uniform(-1.0, 1.0, fluid.shape[0]))
     vel = rng.normal(0.0, 1.0, size=fluid.shape) * vel_scale
     return Scene(

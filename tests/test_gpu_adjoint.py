@@ -12,6 +12,13 @@ Tolerances:
     (dF/dr, the limiter) are larger than the values by a factor of order
     2h/r ~ 10, so 3 steps allow ~1e-3;
   * central differences of the FP64 forward: 1e-6 relative.
+The FP32 comparison does not seed p_w on walls whose fluid support at the
+end is not empty but sums to less than 1e-2 W(0).  For a wall supported by
+a single particle at the rim of its kernel, Eq. (wallPressure) gives
+p_w = p_f + rho_f g.r_wf whatever W_wf, but its backward multiplies the
+FP32 residual p_f + ... - p_w (zero in exact arithmetic) by
+W'/W ~ 1/(1 - q/2), unbounded at the rim: the FP32 gradient of such a
+wall's pressure is noise.  The FP64 comparisons seed every wall.
 """
 import numpy as np
 import pytest
@@ -50,6 +57,20 @@ def reference(sc):
 def seeds(sc, rng):
     return {"x": rng.normal(size=(sc.n_fluid, 3)), "v": rng.normal(size=(sc.n_fluid, 3)),
             "rho": rng.normal(size=sc.n_fluid) * 1e-3, "pw": rng.normal(size=sc.n_wall) * 1e-3}
+
+
+def rim_walls(sc, x, floor=1e-2):
+    """Mask of the walls whose fluid support at positions x is not empty but
+    sums to less than floor W(0) (Wendland C2 in units of W(0):
+    (1 - q/2)^4 (2q + 1))."""
+    from scipy.spatial import cKDTree
+    h = sc.h
+    out = np.zeros(sc.n_wall, bool)
+    for w, fl in enumerate(cKDTree(x).query_ball_point(sc.wall_pos, 2 * h)):
+        if fl:
+            q = np.linalg.norm(x[fl] - sc.wall_pos[w], axis=1) / h
+            out[w] = ((1 - q / 2) ** 4 * (2 * q + 1)).sum() < floor
+    return out
 
 
 def gpu_run(sc, rho0, nsteps, precision, seed=None):
@@ -140,6 +161,10 @@ def test_adjoint_fp32_matches_reference():
     sc = adjoint_scene()
     rho0, normals, sigma0 = reference(sc)
     seed = seeds(sc, np.random.default_rng(5))
+    final, _, _ = A.vjp(sc, normals, sigma0, rho0, 3, DT, seed)
+    rim = rim_walls(sc, np.asarray(final["x"]))
+    assert rim.sum() < 0.1 * sc.n_wall
+    seed["pw"] = np.where(rim, 0.0, seed["pw"])
     _, o, _ = A.vjp(sc, normals, sigma0, rho0, 3, DT, seed)
     sim, _, g = gpu_run(sc, rho0, 3, sph.SPH_FP32, seed)
     compare(g, o, 2e-3, 2e-3)

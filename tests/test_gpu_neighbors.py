@@ -103,12 +103,19 @@ def test_fp64_cells_and_neighbour_sets_bit_exact_after_steps():
     sc = S.dam_break()
     ref = oracle.OracleSim(sc)
     with sph.Simulation(sc, precision=sph.SPH_FP64_PLAIN) as sim:
+        done = 0
         for n in (0, 25, 75):
             if n:
                 sim.step(n)
                 ref.step(n)
+                done += n
             g, o = sim.cells(), ref.cells()
-            assert np.array_equal(g["key_f"], o["key_f"]), n
+            bad = np.nonzero(g["key_f"] != o["key_f"])[0]
+            if len(bad):  # report how close the disagreeing particles are to a face
+                u = (ref.fluid()["x"][bad] - np.asarray(sc.lo)) / (2 * sc.h)
+                face = np.abs(u - np.round(u)).min(axis=1) * 2 * sc.h / sc.dp
+                pytest.fail(f"after {done} steps {len(bad)} keys differ, e.g. particle "
+                            f"{bad[0]}; their distance to a cell face: {np.sort(face)[:5]} dp")
             assert np.array_equal(g["order_f"], o["order_f"].astype(np.int32)), n
             assert np.array_equal(g["start_f"], o["start_f"].astype(np.int32)), n
             gf, gw = check_sets_exact(sim, ref, sc.n_fluid)
@@ -158,8 +165,7 @@ def test_fp32_neighbour_sets_on_the_gpu_state_outside_the_ulp_band():
 def test_fp32_cells_and_sets_against_the_oracle_trajectory():
     """FP32 form against the FP64 oracle's own run (25 and 100 steps): keys
     equal except for particles nearer a cell face than twice the largest
-    position disagreement eps (the lattice start puts whole planes of
-    particles on faces); order and ranges are the (key, id) sort of the keys;
+    position disagreement eps; order and ranges are the (key, id) sort of the keys;
     neighbour sets equal except for pairs whose separation is within 2 eps of
     2h."""
     sc = S.dam_break()
