@@ -153,6 +153,18 @@ typedef struct sph_ctx sph_ctx;
 sph_status sph_create(const sph_params* params, const sph_fluid* fluid,
                       const sph_wall* wall, void* cuda_stream, sph_ctx** out);
 
+/* sph_create with the fluid arrays (pos, vel, rho, phase of *fluid) in
+ * device memory of the current device, e.g. tensors a framework already
+ * holds there: they are copied on the stream (device to device), so the
+ * state never passes through the host (Sec. 3: device-resident state).
+ * The struct itself and the walls stay host memory.  The per-particle
+ * checks of sph_create (finite positions and velocities, rho > 0, phase in
+ * range, one y in 2-D) run as a kernel before any other use, with one
+ * synchronisation; a failure returns SPH_ERR_ARG.  The caller keeps its
+ * arrays.  Other errors as sph_create. */
+sph_status sph_create_device(const sph_params* params, const sph_fluid* fluid,
+                             const sph_wall* wall, void* cuda_stream, sph_ctx** out);
+
 /* Advance nsteps kick-drift-kick steps (Sec. 2.6): reinitialise density if
  * due (Eqs. eqrhosum / eqrhosumnosurface), half kick and drift, re-bin and
  * sort, continuity or summation density and EOS, wall pressure, momentum

@@ -6,7 +6,9 @@ from the given initial state and parameters, tapes ``nsteps`` steps
 pressures as float64 tensors; their backward calls sph_backward, which
 recomputes each step from its checkpoint and runs the hand-written adjoint
 kernels.  The inputs may live on the CPU or the current CUDA device; the
-outputs and gradients live on the device of x0.  Marshalling only: every step
+outputs and gradients live on the device of x0.  On the device the start
+state goes to sph_create_device and outputs and gradients come back as
+device views: no state passes through the host.  Marshalling only: every step
 and every adjoint runs in the CUDA library.
 """
 from __future__ import annotations
@@ -27,11 +29,22 @@ class SPHRun(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x0, v0, rho0, c0, gamma_p, mu, scene, nsteps, dt, precision):
         phases = [dataclasses.replace(ph, mu=float(mu)) for ph in scene.phases]
-        sc = dataclasses.replace(scene, fluid_pos=_np(x0), fluid_vel=_np(v0), c0=float(c0),
-                                 gamma_p=float(gamma_p), phases=phases)
-        sim = sph.Simulation(sc, precision=precision, rho=_np(rho0))
-        sim.tape(int(nsteps), float(dt))
         dev = x0.device
+        if dev.type == "cuda":
+            # device-resident start: sph_create_device copies the tensors on
+            # the device (no trip through the host)
+            sc = dataclasses.replace(scene, c0=float(c0), gamma_p=float(gamma_p), phases=phases)
+            dv = lambda t: t.detach().to(dev, torch.float64).contiguous()  # noqa: E731
+            xs, vs, rs = dv(x0), dv(v0), dv(rho0)
+            ph = None  # one phase: NULL means phase 0 everywhere
+            if len(scene.phases) > 1:
+                ph = torch.as_tensor(np.ascontiguousarray(scene.fluid_phase, np.int32)).to(dev)
+            sim = sph.Simulation.from_device(sc, xs, vs, rs, ph, precision=precision)
+        else:
+            sc = dataclasses.replace(scene, fluid_pos=_np(x0), fluid_vel=_np(v0), c0=float(c0),
+                                     gamma_p=float(gamma_p), phases=phases)
+            sim = sph.Simulation(sc, precision=precision, rho=_np(rho0))
+        sim.tape(int(nsteps), float(dt))
         nf, nw = sim.nf, sim.nw
         if dev.type == "cuda":
             outs = [torch.empty((nf, 3), dtype=torch.float64, device=dev),

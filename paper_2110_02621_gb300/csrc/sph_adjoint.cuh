@@ -222,7 +222,7 @@ __device__ __forceinline__ void wall_continuity_adj(const Cfg<T>& C, const Phase
 static __global__ void k_adj_inverse(int32_t n, const int32_t* __restrict__ id_old, int32_t* __restrict__ inv)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s < n) inv[id_old[s]] = s;
+    if (s < n) inv[SPH_CK(id_old[s], n, CK_SLOT)] = s;
 }
 
 // A = adjoint of a' in total (a' enters a'-state and the final kick)
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(LBLOCK, sizeof(T) == 4 ? 8 : 4) k_adj_continui
             // d' = d~ + dt D, p~ = EOS(d~), rho~ = rho0 + d~
             const T dt_bar = tv.w + rb + pb * eos_dp_dd(P, C, d_i, p_i);
             gc0 += (double)(pb * T(2) * p_i * C.inv_c0);
-            const int s = inv_old[id_new[i]];
+            const int s = SPH_CK(inv_old[SPH_CK(id_new[i], n, CK_SLOT)], n, CK_SLOT);
             T dbar = dt_bar, sbar = T(0);
             if (reinit) {
                 // d~ = R(d, dsig), Eq. (eqrhosum) written on d = rho - rho0

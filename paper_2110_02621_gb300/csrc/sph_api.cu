@@ -26,7 +26,10 @@ sph_status bad(std::string* where, const std::string& msg)
     return SPH_ERR_ARG;
 }
 
-sph_status validate(const sph_params* P, const sph_fluid* F, const sph_wall* W, std::string* msg)
+// fluid_host: the fluid arrays are host memory and are checked here; device
+// arrays are checked by a kernel at create.
+sph_status validate(const sph_params* P, const sph_fluid* F, const sph_wall* W, std::string* msg,
+                    bool fluid_host = true)
 {
     if (!P || !F) return bad(msg, "params and fluid must not be NULL");
     if (!(P->dp > 0) || !(P->h > 0) || !(P->c0 > 0) || !(P->cfl > 0) || !(P->gamma_tait > 0) ||
@@ -66,7 +69,7 @@ sph_status validate(const sph_params* P, const sph_fluid* F, const sph_wall* W, 
     int64_t nw = W ? W->n : 0;
     if (nw < 0 || nw >= (1 << 26)) return bad(msg, "wall.n must be in [0, 2^26)");
     if (nw > 0 && !W->pos) return bad(msg, "wall.pos must not be NULL");
-    for (int64_t i = 0; i < F->n; ++i) {
+    for (int64_t i = 0; fluid_host && i < F->n; ++i) {
         if (!finite3(F->pos + 3 * i)) return bad(msg, "non-finite fluid position");
         if (F->vel && !finite3(F->vel + 3 * i)) return bad(msg, "non-finite fluid velocity");
         if (F->rho && !(F->rho[i] > 0 && std::isfinite(F->rho[i]))) return bad(msg, "fluid rho must be > 0");
@@ -76,8 +79,8 @@ sph_status validate(const sph_params* P, const sph_fluid* F, const sph_wall* W, 
         if (!finite3(W->pos + 3 * i)) return bad(msg, "non-finite wall position");
     if (P->dim == 2) {
         // one plane: every y equal (pairs then have r_y = 0 exactly)
-        const double y0 = F->n > 0 ? F->pos[1] : (nw > 0 ? W->pos[1] : 0.0);
-        for (int64_t i = 0; i < F->n; ++i)
+        const double y0 = F->n > 0 && fluid_host ? F->pos[1] : (nw > 0 ? W->pos[1] : 0.0);
+        for (int64_t i = 0; fluid_host && i < F->n; ++i)
             if (F->pos[3 * i + 1] != y0 || (F->vel && F->vel[3 * i + 1] != 0.0))
                 return bad(msg, "dim = 2: every particle needs the same y and zero y velocity");
         for (int64_t i = 0; i < nw; ++i)
@@ -114,7 +117,34 @@ sph_status sph_create(const sph_params* params, const sph_fluid* fluid, const sp
     sph_ctx* ctx = new (std::nothrow) sph_ctx;
     if (!ctx) return SPH_ERR_OOM;
     ctx->sim = params->precision == SPH_FP64_PLAIN ? sph::make_sim_f64(st) : sph::make_sim_f32(st);
-    s = ctx->sim->create(*params, *fluid, wall ? *wall : empty);
+    s = ctx->sim->create(*params, *fluid, wall ? *wall : empty, false);
+    if (s != SPH_OK) {
+        g_create_error = ctx->sim->err;
+        delete ctx->sim;
+        delete ctx;
+        return s;
+    }
+    *out = ctx;
+    return SPH_OK;
+}
+
+sph_status sph_create_device(const sph_params* params, const sph_fluid* fluid, const sph_wall* wall,
+                             void* cuda_stream, sph_ctx** out)
+{
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out must not be NULL";
+        return SPH_ERR_ARG;
+    }
+    *out = nullptr;
+    sph_status s = validate(params, fluid, wall, &g_create_error, false);
+    if (s != SPH_OK) return s;
+    sph_wall empty{0, nullptr};
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    sph_ctx* ctx = new (std::nothrow) sph_ctx;
+    if (!ctx) return SPH_ERR_OOM;
+    ctx->sim = params->precision == SPH_FP64_PLAIN ? sph::make_sim_f64(st) : sph::make_sim_f32(st);
+    s = ctx->sim->create(*params, *fluid, wall ? *wall : empty, true);
     if (s != SPH_OK) {
         g_create_error = ctx->sim->err;
         delete ctx->sim;

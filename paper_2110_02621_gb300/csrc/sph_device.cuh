@@ -49,10 +49,32 @@ struct Cfg {
     double g64[3];          // g in FP64 (for the body force of a moving tank)
     double ex_amp[3], ex_w; // rigid tank motion x = amp sin(w t), w = 2 pi f (Sec. 4.2)
     int32_t nx, ny, nz, n_cells;
+    int32_t nf, nw;         // fluid and wall particle counts (index checks)
     int32_t periodic;       // bit d: axis d wraps (n_d cells of side cs make the period)
     int32_t n_phases;
     PhaseK<T> ph[2];
 };
+
+// ------------------------------------------------------------ index checks
+// Debug build (-DSPH_CHECK): an index read from memory (a list entry, a cell
+// key, a cell range, a sort slot) is checked before it addresses anything.
+// One out of range sets a bit of the translation unit's check word and is
+// replaced by 0, so the kernel carries on without a wild access; the host
+// reads the word after each synchronising call and reports SPH_ERR_CUDA.
+// Without the flag SPH_CK(i, n, bit) is i.
+constexpr unsigned CK_FLIST = 1, CK_WLIST = 2, CK_CELL = 4, CK_RANGE = 8, CK_SLOT = 16;
+#ifdef SPH_CHECK
+static __device__ unsigned int g_sph_check;
+__device__ __forceinline__ int32_t sph_ck(int32_t i, int32_t n, unsigned bit)
+{
+    if ((uint32_t)i < (uint32_t)n) return i;
+    atomicOr(&g_sph_check, bit);
+    return 0;
+}
+#define SPH_CK(i, n, bit) ::sph::sph_ck((i), (n), (bit))
+#else
+#define SPH_CK(i, n, bit) (i)
+#endif
 
 // ---------------------------------------------------------------- rounding
 // The drift is evaluated twice (when counting cells and when moving the

@@ -34,7 +34,8 @@ cudaError_t bin_sort_run(const double* pos, int32_t n, const double lo[3], doubl
 
 struct SimBase {
     virtual ~SimBase() {}
-    virtual sph_status create(const sph_params& P, const sph_fluid& F, const sph_wall& W) = 0;
+    // fluid_dev: F's arrays are device memory (checked by a kernel), else host
+    virtual sph_status create(const sph_params& P, const sph_fluid& F, const sph_wall& W, bool fluid_dev) = 0;
     virtual sph_status step(int32_t nsteps, double dt, double* dt_out) = 0;
     virtual sph_status step_async(int32_t nsteps, double dt) = 0;
     virtual sph_status sync(double* dt_out) = 0;

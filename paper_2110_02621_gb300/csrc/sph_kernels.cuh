@@ -148,7 +148,7 @@ static __global__ void k_scatter(int32_t n, int32_t n_cells, const int4* __restr
     if (s >= n) return;
     if (s == 0 && vmax_reset) *vmax_reset = 0ull;
     int key = newcell[s].w;
-    int t = start[key < 0 ? n_cells : key] + rank[s];
+    int t = SPH_CK(start[key < 0 ? n_cells : SPH_CK(key, n_cells, CK_CELL)] + rank[s], n, CK_SLOT);
     tmp_src[t] = s;
     tmp_id[t] = id[s];
 }
@@ -160,6 +160,7 @@ __device__ __forceinline__ int32_t sorted_slot(int32_t t, int32_t key, int32_t n
                                                const int32_t* __restrict__ tmp_id)
 {
     if (key < 0) return t;  // outside the grid: order inside the bucket unspecified
+    key = SPH_CK(key, n_cells, CK_CELL);
     int b = start[key], e = start[key + 1];
     int my = tmp_id[t], r = 0;
     for (int u = b; u < e; ++u) r += (tmp_id[u] < my);
@@ -200,9 +201,9 @@ __global__ void k_gather(Cfg<T> C, int32_t n, const int32_t* __restrict__ start,
 {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    int s = tmp_src[t];
+    int s = SPH_CK(tmp_src[t], n, CK_SLOT);
     int4 c = newcell[s];
-    int dst = sorted_slot(t, c.w, C.n_cells, start, tmp_id);
+    int dst = SPH_CK(sorted_slot(t, c.w, C.n_cells, start, tmp_id), n, CK_SLOT);
     T dt = *d_dt;
     V4<T> p = pos[s], v = vel[s], a = acc[s], cm = comp[s];
     int4 c_old = cell[s];

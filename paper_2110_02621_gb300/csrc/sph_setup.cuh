@@ -58,6 +58,28 @@ __device__ __forceinline__ double hydro_p(const InitCfg& I, int k, double z)
     return p;
 }
 
+// Checks of fluid inputs that are device memory (sph_create_device), the
+// same as sph_create makes on the host: finite positions and velocities,
+// finite rho > 0, phase in [0, n_phases), and in 2-D one y for every
+// particle (y0, or the first particle's y) with zero y velocity.  Any failure
+// sets bit 0 of *bad.
+static __global__ void k_check_fluid(int32_t n, const double* __restrict__ x, const double* __restrict__ v,
+                                     const double* __restrict__ rho, const int32_t* __restrict__ phase,
+                                     int32_t n_phases, int32_t dim2, double y0, int32_t y0_first, int32_t* bad)
+{
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    bool ok = isfinite(x[3 * i]) && isfinite(x[3 * i + 1]) && isfinite(x[3 * i + 2]);
+    if (v) ok = ok && isfinite(v[3 * i]) && isfinite(v[3 * i + 1]) && isfinite(v[3 * i + 2]);
+    if (rho) ok = ok && rho[i] > 0.0 && isfinite(rho[i]);
+    if (phase) ok = ok && phase[i] >= 0 && phase[i] < n_phases;
+    if (dim2) {
+        const double yr = y0_first ? x[1] : y0;
+        ok = ok && x[3 * i + 1] == yr && (!v || v[3 * i + 1] == 0.0);
+    }
+    if (!ok) atomicOr(bad, 1);
+}
+
 // Fluid in input order: cell, offset, velocity, density excess and pressure;
 // counts the cell occupancy for the first sort.
 template <class T>

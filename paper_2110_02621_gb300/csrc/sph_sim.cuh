@@ -93,6 +93,7 @@ Cfg<T> make_cfg(const sph_params& P, const int32_t dims[3])
     double alpha = wendland_alpha(h, dim);
     C.h = (T)h;
     C.rc2 = (T)(cs * cs);
+    C.nf = C.nw = 0;
     C.cs = (T)cs;
     C.alpha = (T)alpha;
     C.fcoef = (T)(-5.0 * alpha / (h * h));
@@ -172,7 +173,7 @@ class Sim final : public SimBase {
         if (host_status_) cudaFreeHost(host_status_);
     }
 
-    sph_status create(const sph_params& P, const sph_fluid& F, const sph_wall& Wl) override
+    sph_status create(const sph_params& P, const sph_fluid& F, const sph_wall& Wl, bool fluid_dev) override
     {
         P_ = P;
         cs_ = 2.0 * P.h;
@@ -186,6 +187,8 @@ class Sim final : public SimBase {
         }
         C_ = make_cfg<T>(P, dims_);
         D_ = make_cfg<double>(P, dims_);
+        C_.nf = D_.nf = (int32_t)F.n;
+        C_.nw = D_.nw = (int32_t)Wl.n;
         for (int d = 0; d < 3; ++d) I_.lo[d] = P.lo[d];
         I_.cs = cs_;
         I_.gz = P.g[2];
@@ -246,22 +249,42 @@ class Sim final : public SimBase {
         double *x_in = nullptr, *v_in = nullptr, *r_in = nullptr;
         int32_t* ph_in = nullptr;
         if (nf_ > 0) {
+            // device inputs are copied too: the caller keeps its arrays
+            const cudaMemcpyKind kind = fluid_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
             size_t b3 = sizeof(double) * 3 * (size_t)nf_;
             SPH_CUDA(cudaMallocAsync(&x_in, b3, stream));
-            SPH_CUDA(cudaMemcpyAsync(x_in, F.pos, b3, cudaMemcpyHostToDevice, stream));
+            SPH_CUDA(cudaMemcpyAsync(x_in, F.pos, b3, kind, stream));
             if (F.vel) {
                 SPH_CUDA(cudaMallocAsync(&v_in, b3, stream));
-                SPH_CUDA(cudaMemcpyAsync(v_in, F.vel, b3, cudaMemcpyHostToDevice, stream));
+                SPH_CUDA(cudaMemcpyAsync(v_in, F.vel, b3, kind, stream));
             }
             if (F.rho) {
                 SPH_CUDA(cudaMallocAsync(&r_in, sizeof(double) * (size_t)nf_, stream));
-                SPH_CUDA(cudaMemcpyAsync(r_in, F.rho, sizeof(double) * (size_t)nf_, cudaMemcpyHostToDevice,
-                                         stream));
+                SPH_CUDA(cudaMemcpyAsync(r_in, F.rho, sizeof(double) * (size_t)nf_, kind, stream));
             }
             if (F.phase) {
                 SPH_CUDA(cudaMallocAsync(&ph_in, sizeof(int32_t) * (size_t)nf_, stream));
-                SPH_CUDA(cudaMemcpyAsync(ph_in, F.phase, sizeof(int32_t) * (size_t)nf_,
-                                         cudaMemcpyHostToDevice, stream));
+                SPH_CUDA(cudaMemcpyAsync(ph_in, F.phase, sizeof(int32_t) * (size_t)nf_, kind, stream));
+            }
+            if (fluid_dev) {
+                // the host checks of sph_create, on the device, before any use
+                SPH_CUDA(cudaMemsetAsync(d_flags_, 0, sizeof(int32_t), stream));
+                k_check_fluid<<<grid_for(nf_), BLOCK, 0, stream>>>(
+                    nf_, x_in, v_in, r_in, ph_in, P.n_phases, P.dim == 2 ? 1 : 0, nw_ > 0 ? Wl.pos[1] : 0.0,
+                    nw_ > 0 ? 0 : 1, d_flags_);
+                SPH_LAUNCH();
+                SPH_CUDA(cudaMemcpyAsync(&host_status_->flags, d_flags_, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                         stream));
+                SPH_CUDA(cudaStreamSynchronize(stream));
+                if (host_status_->flags) {
+                    for (void* p : {(void*)x_in, (void*)v_in, (void*)r_in, (void*)ph_in})
+                        if (p) SPH_CUDA(cudaFreeAsync(p, stream));
+                    SPH_CUDA(cudaStreamSynchronize(stream));
+                    err = P.dim == 2 ? "fluid inputs: non-finite position or velocity, rho <= 0, phase out of range, "
+                                       "or (2-D) a y or y velocity that differs"
+                                     : "fluid inputs: non-finite position or velocity, rho <= 0 or phase out of range";
+                    return SPH_ERR_ARG;
+                }
             }
         }
         SPH_CUDA(cudaMemsetAsync(counts_, 0, sizeof(int32_t) * (size_t)(n_cells_ + 1), stream));
@@ -320,6 +343,7 @@ class Sim final : public SimBase {
         SPH_CUDA(cudaMemcpyAsync(&host_status_->w_in, wstart_ + n_cells_, sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, stream));
         SPH_CUDA(cudaStreamSynchronize(stream));
+        if (sph_status sc = index_check(); sc != SPH_OK) return sc;
         if (host_status_->n_in != nf_ || host_status_->w_in != nw_) {
             char buf[160];
             snprintf(buf, sizeof buf, "%d fluid and %d wall particles lie outside the grid [lo, hi)",
@@ -371,6 +395,28 @@ class Sim final : public SimBase {
         return SPH_OK;
     }
 
+    // The check word of the index-checking build (-DSPH_CHECK): a set bit
+    // names the kind of index found out of range since the last call.
+    sph_status index_check()
+    {
+#ifdef SPH_CHECK
+        unsigned w = 0;
+        const unsigned zero = 0;
+        SPH_CUDA(cudaMemcpyFromSymbolAsync(&w, g_sph_check, sizeof w, 0, cudaMemcpyDeviceToHost, stream));
+        SPH_CUDA(cudaMemcpyToSymbolAsync(g_sph_check, &zero, sizeof zero, 0, cudaMemcpyHostToDevice, stream));
+        SPH_CUDA(cudaStreamSynchronize(stream));
+        if (w) {
+            char buf[160];
+            snprintf(buf, sizeof buf,
+                     "index check: out of range (bits 0x%x: 1 fluid list, 2 wall list, 4 cell, 8 range, 16 slot)", w);
+            err = buf;
+            dead = true;
+            return SPH_ERR_CUDA;
+        }
+#endif
+        return SPH_OK;
+    }
+
     // read the error word, the in-grid count and the last dt after a run of
     // steps (one synchronisation)
     sph_status finish_steps(double* dt_out)
@@ -382,6 +428,7 @@ class Sim final : public SimBase {
         SPH_CUDA(cudaMemcpyAsync(&host_status_->dt, d_dt_, sizeof(T), cudaMemcpyDeviceToHost, stream));
         SPH_CUDA(cudaStreamSynchronize(stream));
         if (dt_out) *dt_out = (double)host_status_->dt;
+        if (sph_status sc = index_check(); sc != SPH_OK) return sc;
         if (host_status_->flags & 1) {
             err = "non-finite acceleration";
             dead = true;
@@ -661,7 +708,7 @@ class Sim final : public SimBase {
                 SPH_CUDA(cudaMemcpyAsync(grad.rho, orho, sizeof(double) * nf, cudaMemcpyDeviceToHost, stream));
         }
         SPH_CUDA(cudaStreamSynchronize(stream));
-        return SPH_OK;
+        return index_check();
     }
 
     sph_status profile(uint32_t mask) override
@@ -777,6 +824,7 @@ class Sim final : public SimBase {
         SPH_CUDA(cudaStreamSynchronize(stream));
         SPH_CUDA(cudaFreeAsync(lc, stream));
         SPH_CUDA(cudaFreeAsync(dof, stream));
+        if (sph_status sc = index_check(); sc != SPH_OK) return sc;
         if (overflow) {
             overflow[0] = (int64_t)hof[0];
             overflow[1] = (int64_t)hof[1];

@@ -131,7 +131,8 @@ __device__ __forceinline__ void scan_row_wrapped(const Cfg<T>& C, int row, int c
     int v = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const int b = __ldg(start + row + cells[k]), e = __ldg(start + row + cells[k] + 1);
+        const int e = __ldg(start + SPH_CK(row + cells[k] + 1, C.n_cells + 1, CK_CELL));
+        const int b = SPH_CK(__ldg(start + row + cells[k]), e + 1, CK_RANGE);
 #pragma unroll 1
         for (int j = b + ((l - v) % NL + NL) % NL; j < e; j += NL) {
             const V4<T> pj = pts[j];
@@ -171,7 +172,8 @@ __device__ __forceinline__ void scan_share(const Cfg<T>& C, const int4& c, const
                 scan_row_wrapped<LP>(C, row, c.x, start, pts, l, xl, o.x, xr, ys, zs, cyz, fn);
                 continue;
             }
-            const int b = __ldg(start + row + xa), e = __ldg(start + row + xb + 1);
+            const int rb = SPH_CK(row + xa, C.n_cells, CK_CELL), re = SPH_CK(row + xb + 1, C.n_cells + 1, CK_CELL);
+            const int e = __ldg(start + re), b = SPH_CK(__ldg(start + rb), e + 1, CK_RANGE);
             const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
 #pragma unroll 4
             for (int j = b + l; j < e; j += LP) {
@@ -189,9 +191,10 @@ __device__ __forceinline__ void scan_share(const Cfg<T>& C, const int4& c, const
 // scan_share for the list builder: each row's three cells in turn with a
 // constant x shift (fewer instructions per candidate; larger code).
 // Lane l's share (every LP-th candidate) of the 27 cells around cell c of a
-// sorted set with cell ranges start[]: fn(j, rx, ry, rz, r2, code) for every
-// candidate with 0 < r^2 < (2h)^2, o = the target's offset, code = the
-// 6-bit cell shift of j.
+// sorted set with cell ranges start[]: fn(j, code, hit) for every
+// candidate, hit = (0 < r^2 < (2h)^2), o = the target's offset, code = the
+// 6-bit cell shift of j.  The callback runs for every candidate, so that the
+// builder records hits with predicated instructions instead of a branch.
 // Only the rows whose bit (dz + 1) 3 + (dy + 1) is set in rows are walked.
 template <bool PER, class T, class Fn>
 __device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const V4<T>& o,
@@ -215,10 +218,12 @@ __device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const 
             const int row = (z * C.ny + y) * C.nx;
             const int cyz = (dy + 1) << 2 | (dz + 1) << 4;
             if (wrap_x) {
-                scan_row_wrapped<LP>(C, row, c.x, start, pts, l, xl, o.x, xr, ys, zs, cyz, fn);
+                scan_row_wrapped<LP>(C, row, c.x, start, pts, l, xl, o.x, xr, ys, zs, cyz,
+                                     [&](int j, T, T, T, T, int code) { fn(j, code, true); });
                 continue;
             }
-            const int b = __ldg(start + row + xa), e = __ldg(start + row + xb + 1);
+            const int rb = SPH_CK(row + xa, C.n_cells, CK_CELL), re = SPH_CK(row + xb + 1, C.n_cells + 1, CK_CELL);
+            const int e = __ldg(start + re), b = SPH_CK(__ldg(start + rb), e + 1, CK_RANGE);
             const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
             // the row's three cells in turn, each with its constant x shift;
             // j runs on across them, so the lanes' shares stay interleaved
@@ -229,7 +234,7 @@ __device__ __forceinline__ void scan_rows(const Cfg<T>& C, const int4& c, const 
                     const V4<T> pj = pts[j];
                     const T rx = xs - pj.x, ry = ys - pj.y, rz = zs - pj.z;
                     const T r2 = dist2(rx, ry, rz);
-                    if (r2 < C.rc2 && r2 > T(0)) fn(j, rx, ry, rz, r2, code);
+                    fn(j, code, r2 < C.rc2 && r2 > T(0));
                 }
             };
             segment(b1, xl, cyz);
@@ -268,7 +273,8 @@ __device__ __forceinline__ void scan_compact(const Cfg<T>& C, const int4& c, con
                 scan_row_wrapped<NL>(C, row, c.x, start, pts, l, xl, o.x, xr, ys, zs, cyz, fn);
                 continue;
             }
-            const int b = __ldg(start + row + xa), e = __ldg(start + row + xb + 1);
+            const int rb = SPH_CK(row + xa, C.n_cells, CK_CELL), re = SPH_CK(row + xb + 1, C.n_cells + 1, CK_CELL);
+            const int e = __ldg(start + re), b = SPH_CK(__ldg(start + rb), e + 1, CK_RANGE);
             const int b1 = __ldg(start + row + c.x), b2 = __ldg(start + row + c.x + 1);
 #pragma unroll 1
             for (int j = b + l; j < e; j += NL) {
@@ -323,8 +329,10 @@ __global__ void k_wall_rows(Cfg<T> C, int32_t n_cells, const int32_t* __restrict
 }
 
 // --------------------------------------------------------- neighbour lists
+// Ten blocks per SM (48 registers, no spills): measured 64.3 against 65.7 us
+// at 80 k particles and 5.33 against 5.66 ms at 10.35 M without the bound.
 template <class T, bool PER>
-__global__ void __launch_bounds__(LBLOCK) k_neighbors(
+__global__ void __launch_bounds__(LBLOCK, 10) k_neighbors(
     Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
     const uint16_t* __restrict__ wrows, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ wpos,
     const int4* __restrict__ cell, int32_t* __restrict__ nbf, int32_t* __restrict__ nbw,
@@ -338,23 +346,23 @@ __global__ void __launch_bounds__(LBLOCK) k_neighbors(
     if (c.w >= 0) {
         const V4<T> o = pos[i];
         const int tag = *d_tag;
-        const size_t stride = (size_t)n * LP;
-        size_t at = t;
-        scan_rows<PER>(C, c, o, fstart, pos, l, [&](int j, T, T, T, T, int code) {
-            if (nf < SUBF) nbf[at] = (j << 6) | code;
-            at += stride;
-            ++nf;
+        const uint32_t stride = (uint32_t)n * LP;
+        // entry k of this lane's sub-list sits at k stride (one wide
+        // multiply-add per store)
+        int32_t* const qf = nbf + t;
+        int32_t* const qw = nbw + t;
+        scan_rows<PER>(C, c, o, fstart, pos, l, [&](int j, int code, bool hit) {
+            if (hit && nf < SUBF) qf[(size_t)(uint32_t)nf * stride] = (j << 6) | code;
+            nf += hit;
         });
-        at = t;
-        const unsigned wr = __ldg(wrows + c.w);
+        const unsigned wr = __ldg(wrows + SPH_CK(c.w, C.n_cells, CK_CELL));
         if (wr)
             scan_rows<PER>(
                 C, c, o, wstart, wpos, l,
-                [&](int w, T, T, T, T, int code) {
-                    if (nw < SUBW) nbw[at] = (w << 6) | code;
-                    at += stride;
-                    ++nw;
-                    wtag[w] = tag;
+                [&](int w, int code, bool hit) {
+                    if (hit && nw < SUBW) qw[(size_t)(uint32_t)nw * stride] = (w << 6) | code;
+                    if (hit) wtag[w] = tag;
+                    nw += hit;
                 },
                 wr);
     }
@@ -380,7 +388,7 @@ __device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t,
             const int e = __ldg(nbf + at);
             T sx, sy, sz;
             shift_of(C, e, sx, sy, sz);
-            const int j = e >> 6;
+            const int j = SPH_CK(e >> 6, C.nf, CK_FLIST);
             const V4<T> pj = pos[j];
             const T rx = (pi.x - sx) - pj.x, ry = (pi.y - sy) - pj.y, rz = (pi.z - sz) - pj.z;
             ff(j, pj, rx, ry, rz, dist2(rx, ry, rz));
@@ -396,7 +404,7 @@ __device__ __forceinline__ void for_neighbors(const Cfg<T>& C, int32_t n, int t,
             const int e = __ldg(nbw + at);
             T sx, sy, sz;
             shift_of(C, e, sx, sy, sz);
-            const int w = e >> 6;
+            const int w = SPH_CK(e >> 6, C.nw, CK_WLIST);
             const V4<T> pw = wpos[w];
             const T rx = (pi.x - sx) - pw.x, ry = (pi.y - sy) - pw.y, rz = (pi.z - sz) - pw.z;
             fw(w, pw, rx, ry, rz, dist2(rx, ry, rz));

@@ -29,7 +29,8 @@ EXPORTS = ("sph_create", "sph_step", "sph_reinit_density", "sph_get_state",
            "sph_last_error", "sph_destroy", "sph_bin_sort", "sph_bin_sort_noalloc",
            "sph_profile", "sph_profile_read", "sph_tape", "sph_backward", "sph_step_async",
            "sph_sync", "sph_diagnostics_async", "sph_set_excitation", "sph_time",
-           "sph_probe_pressure", "sph_gauge_height", "sph_tape_budget", "sph_get_neighbors")
+           "sph_probe_pressure", "sph_gauge_height", "sph_tape_budget", "sph_get_neighbors",
+           "sph_create_device")
 SPH_GAUGE_MAX_SAMPLES = 65536
 SPH_GAUGE_MAX_LINES = 65535
 SPH_ERR_CAPACITY = 8
@@ -91,17 +92,32 @@ def library_path() -> str:
     return _build.LIB
 
 
+_lib_path = None
+
+
+def use_library(path: Optional[str]) -> Optional[str]:
+    """Bind to another build of the library from now on (e.g. the
+    index-checking build, build.build(check=True)); None = the default.
+    Returns the previous choice.  Contexts of the previous library must be
+    destroyed first."""
+    global _lib, _lib_path
+    prev = _lib_path
+    _lib, _lib_path = None, path
+    return prev
+
+
 def lib() -> C.CDLL:
     """Load libsph_gb300.so; raises if it has not been built."""
     global _lib
     if _lib is None:
-        path = _build.LIB
+        path = _lib_path or _build.LIB
         if not os.path.exists(path):
             raise ImportError(f"{path} is missing: build it with "
                               "`python -m paper_2110_02621_gb300.build` (nvcc, sm_103a)")
         L = C.CDLL(path)
         p, i32, i64, d, st = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_int
         L.sph_create.argtypes = [p, p, p, p, C.POINTER(p)]
+        L.sph_create_device.argtypes = [p, p, p, p, C.POINTER(p)]
         L.sph_step.argtypes = [p, i32, d, p]
         L.sph_reinit_density.argtypes = [p]
         L.sph_get_state.argtypes = [p, p, i32]
@@ -182,6 +198,16 @@ def sph_create(params: sph_params, fluid: sph_fluid, wall: Optional[sph_wall],
     st = lib().sph_create(C.byref(params), C.byref(fluid),
                           C.byref(wall) if wall is not None else None,
                           C.c_void_p(stream), C.byref(ctx))
+    return st, ctx
+
+
+def sph_create_device(params: sph_params, fluid: sph_fluid, wall: Optional[sph_wall],
+                      stream: int = 0):
+    """sph_create with fluid arrays that are device memory."""
+    ctx = C.c_void_p()
+    st = lib().sph_create_device(C.byref(params), C.byref(fluid),
+                                 C.byref(wall) if wall is not None else None,
+                                 C.c_void_p(stream), C.byref(ctx))
     return st, ctx
 
 
@@ -320,6 +346,30 @@ class Simulation:
         st, ctx = sph_create(self.params, fluid, wall, self.stream)
         _check(st, None)
         self.ctx = ctx
+
+    @classmethod
+    def from_device(cls, scene, x, v=None, rho=None, phase=None, precision: int = SPH_FP32,
+                    stream: Optional[int] = None):
+        """A context whose fluid comes from device arrays (objects exposing
+        data_ptr(): x (n, 3) and v (n, 3) float64, rho (n,) float64, phase
+        (n,) int32, all contiguous on the current device; sph_create_device).
+        The scene supplies the walls and every parameter; its own fluid
+        arrays are not used.  The arrays are copied on the stream, which
+        create synchronises, so they may be freed once this returns."""
+        self = cls.__new__(cls)
+        self.scene = scene
+        self.precision = precision
+        self.nf, self.nw = int(x.shape[0]), scene.n_wall
+        self._xw = np.ascontiguousarray(scene.wall_pos, np.float64).reshape(-1, 3)
+        self.params = make_params(scene, precision)
+        dp = lambda a: None if a is None else a.data_ptr()  # noqa: E731
+        fluid = sph_fluid(self.nf, dp(x), dp(v), dp(rho), dp(phase))
+        wall = sph_wall(self.nw, _ptr(self._xw))
+        self.stream = current_stream_handle() if stream is None else stream
+        st, ctx = sph_create_device(self.params, fluid, wall, self.stream)
+        _check(st, None)
+        self.ctx = ctx
+        return self
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -199,3 +199,28 @@ def test_binning_refuses_grids_beyond_the_scan(lib, fn, dims):
     dummy = 1 << 20  # never dereferenced: validation comes first
     st = getattr(sph, fn)(dummy, 10, (0.0, 0.0, 0.0), 0.013, dims, dummy, dummy, dummy, 0)
     assert st == sph.SPH_ERR_ARG
+
+
+DEVICE_SIDE = ("velocity", "rho must be > 0", "phase out of range")
+
+
+@pytest.mark.parametrize("what,spoil,message", [r for r in REJECTIONS if r[2] not in DEVICE_SIDE],
+                         ids=[r[0] for r in REJECTIONS if r[2] not in DEVICE_SIDE])
+def test_create_device_refuses_on_the_host_before_any_cuda_call(lib, what, spoil, message):
+    """sph_create_device applies the same host-side rules as sph_create
+    (everything but the per-particle checks, which it runs on the device) and
+    refuses before any CUDA call."""
+    import numpy as np
+    from paper_2110_02621_gb300 import scenes
+    sc = scenes.still_water_tank(n_fluid=(3, 3, 3))
+    P = sph.make_params(sc)
+    keep = {"pos": np.ascontiguousarray(sc.fluid_pos), "vel": np.zeros((sc.n_fluid, 3)),
+            "rho": np.full(sc.n_fluid, 1000.0), "phase": np.zeros(sc.n_fluid, np.int32),
+            "wall": np.ascontiguousarray(sc.wall_pos)}
+    F = sph.sph_fluid(sc.n_fluid, keep["pos"].ctypes.data, keep["vel"].ctypes.data, keep["rho"].ctypes.data,
+                      keep["phase"].ctypes.data)
+    W = sph.sph_wall(len(keep["wall"]), keep["wall"].ctypes.data)
+    spoil(P, F, W, keep)
+    st, ctx = sph.sph_create_device(P, F, W)
+    assert st == sph.SPH_ERR_ARG and not ctx.value, what
+    assert message in sph.sph_last_error(None), (what, sph.sph_last_error(None))

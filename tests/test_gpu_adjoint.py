@@ -315,11 +315,16 @@ def test_tape_refusals():
     s3.close()
 
 
-def test_autograd_function_matches_the_reference():
+def test_autograd_function_matches_the_reference(monkeypatch):
     """torch.autograd through SPHRun (device tensors) against the oracle's
-    gradient of the same loss."""
+    gradient of the same loss.  The device path never converts a tensor to a
+    host array (the host marshalling helper raises if it is called)."""
     import torch
     from paper_2110_02621_gb300 import autograd as AG
+
+    def no_host_copy(t):
+        raise AssertionError("device tensors went through the host")
+    monkeypatch.setattr(AG, "_np", no_host_copy)
     sc = adjoint_scene()
     rho0, normals, sigma0 = reference(sc)
     dev = torch.device("cuda")
