@@ -68,7 +68,11 @@ typedef struct {
     int32_t reinit;  /* SPH_REINIT_FREE_SURFACE: Eq. (eqrhosum);              *
                       * SPH_REINIT_INTERNAL: Eq. (eqrhosumnosurface)         */
     int32_t penalty; /* 1: penalty force F_p, Eq. (SPH_penaltyMethodTerm),   *
-                      * on this phase's wall interactions                    */
+                      * on this phase's wall interactions; delta of Eq.      *
+                      * (deltaForPenalty) is the signed distance 2 (r_i -   *
+                      * r_w).n_w / dx (a barrier behind the wall particle's *
+                      * plane), through wall particles that have fluid      *
+                      * within 2h on their normal's side in the step        */
 } sph_phase;
 
 typedef struct {

@@ -244,9 +244,11 @@ def wall_pressure(x, rho, p, P: Params, c0, wpairs, nw):
 def momentum(x, v, rho, p, pw, rhow, P: Params, c0, gamma_p, mu, pairs):
     """Eq. (SPH_star_momentumConservation): -2 sum_j m_j p*/(rho_i rho_j) grad_i W_ij
     (fluid p* from Eq. (RSsolution) with the limiter, wall p* from Eq. (RSatWall)),
-    the penalty force F_p (delta = 2|r_iw.n_w|/dx, lambda = (1-delta)^2/dx for
-    delta < 1, P = gamma_p lambda |p_i e_iw.n_w|, times dx^3 |r|^-2 dW/dr), the
-    Morris viscosity with mu_i + mu_j, and g."""
+    the penalty force F_p (delta = 2 r_iw.n_w/dx signed, lambda =
+    (1-delta)^2/dx for delta < 1, P = gamma_p lambda |p_i e_iw.n_w|, times
+    dx^3 |r|^-2 dW/dr) through the fluid-facing wall particles (some fluid of
+    their support on the side the normal points to), the Morris viscosity
+    with mu_i + mu_j, and g."""
     (fi, fj), (wi, ww) = pairs
     m = P.rho0 * P.dp ** 3
     eta2 = 0.01 * P.h ** 2
@@ -273,11 +275,13 @@ def momentum(x, v, rho, p, pw, rhow, P: Params, c0, gamma_p, mu, pairs):
     a = a.index_add(0, wi, kv[:, None] * v[wi])
     if P.penalty:
         nw_ = P.normals[ww]
+        rn = (rij * nw_).sum(dim=1)                      # r_iw . n_w
+        facing = torch.zeros(P.normals.shape[0], dtype=F64).index_add(0, ww, (rn > 0.0).to(F64)) > 0.0
         e = -rij / r[:, None]
         en = (e * nw_).sum(dim=1)
         dx = P.dp
-        delta = 2.0 * r / dx * torch.abs(en)
-        act = (delta < 1.0) & (r > 1e-6 * dx)
+        delta = 2.0 * rn / dx
+        act = facing[ww] & (delta < 1.0) & (r > 1e-6 * dx)
         lam = torch.where(act, (1.0 - delta) ** 2 / dx, torch.zeros_like(delta))
         Ppen = gamma_p * lam * torch.abs(p_i * en)
         k = -2.0 * m / (rho_i * rho_w) * Ppen * dx ** 3 / (r * r) * dWdr(r, P.h)

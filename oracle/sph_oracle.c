@@ -20,13 +20,19 @@
  *     the edge of its domain p > -rho^0 c^2/gamma, and extrapolations that
  *     average fluid torn to half its density pass it);
  *     walls have zero velocity;
- *   - penalty (Eq. penaltyMethodTerm): delta = 2 |(r_i - r_w).n_w| / dx,
- *     the distance of i from the wall particle's tangent plane in units of
- *     dx/2 (read literally, e_iw.n_w < 0 on the fluid side switches the
- *     penalty on for every wall neighbour at rest, and the signed distance
- *     switches it on behind the far-side normals of deeper wall layers);
- *     the printed factors lambda = (1 - delta)^2 / dx and |r_iw|^-2 leave
- *     F_p with three surplus inverse lengths, which the factor dx^3 restores;
+ *   - penalty (Eq. penaltyMethodTerm): delta = 2 (r_i - r_w).n_w / dx, the
+ *     signed distance of i from the wall particle's tangent plane in units of
+ *     dx/2, positive on the side n_w points to (e_iw of Eq. deltaForPenalty
+ *     taken from w to i; with e_iw from i to w, delta < 0 on the fluid side
+ *     and lambda would grow with the distance from the wall).  lambda then
+ *     rises from 0 at dx/2 in front of the plane and keeps rising behind it:
+ *     a barrier.  The penalty acts through a wall particle only while fluid
+ *     lies within 2h on the side its normal points to (the fluid-facing
+ *     particles): Eq. (normalVectors), a sum over walls alone, turns the
+ *     normals of the outer wall layers away from the fluid, and a signed
+ *     delta would switch the penalty on at rest through them.  The printed
+ *     factors lambda = (1 - delta)^2 / dx and |r_iw|^-2 leave F_p with
+ *     three surplus inverse lengths, which the factor dx^3 restores;
  *   - density reinitialisation: free-surface form for continuity-density
  *     phases, internal form for summation-density phases; sigma sums over
  *     the particle's own phase and walls (continuity phases) or over all
@@ -64,6 +70,7 @@ struct orc_sim {
     double *x, *v, *rho, *p, *a, *drho_dt, *sigma;
     int32_t* phase;
     double *xw, *pw, *rhow, *nwall; /* rhow: [nw*2] per fluid phase */
+    int* wfront;                    /* 1: fluid within 2h on the normal's side (penalty) */
     /* cell-linked list */
     int32_t nc[3];
     double cs;
@@ -348,8 +355,10 @@ static void wall_normals(orc_sim* s)
 /* wall dummy pressure, Eq. (wallPressure) with a_w = 0 (fixed walls):
  *   p_w = sum_f (p_f + rho_f (g - a_w).r_wf) w_wf / sum_f w_wf,
  *   r_wf = r_w - r_f,  w_wf = W_wf (one phase) or W_wf / rho_f (several).
- * Empty support: p_w = 0.  Wall density rho_w = EOS^-1(p_w) per phase. */
-typedef struct { const orc_sim* s; double num, den; } wallp_ctx;
+ * Empty support: p_w = 0.  Wall density rho_w = EOS^-1(p_w) per phase.
+ * The same pass marks the fluid-facing wall particles of the penalty: some
+ * fluid f of the support with (r_f - r_w).n_w > 0. */
+typedef struct { const orc_sim* s; int64_t w; double num, den; int front; } wallp_ctx;
 
 static void wallp_visit(void* vctx, int64_t f, const double rwf[3], double r)
 {
@@ -361,16 +370,19 @@ static void wallp_visit(void* vctx, int64_t f, const double rwf[3], double r)
     double gr = s->geff[0] * rwf[0] + s->geff[1] * rwf[1] + s->geff[2] * rwf[2];
     c->num += (s->p[f] + s->rho[f] * gr) * w;
     c->den += w;
+    const double* n = s->nwall + 3 * c->w;
+    if (rwf[0] * n[0] + rwf[1] * n[1] + rwf[2] * n[2] < 0.0) c->front = 1;
 }
 
 static void wall_pressure(orc_sim* s)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t w = 0; w < s->nw; w++) {
-        wallp_ctx c = {s, 0.0, 0.0};
+        wallp_ctx c = {s, w, 0.0, 0.0, 0};
         for_neighbors(s, s->xw + 3 * w, s->x, s->order_f, s->start_f, wallp_visit, &c);
         double pw = (c.den > 0.0) ? c.num / c.den : 0.0;
         s->pw[w] = pw;
+        s->wfront[w] = c.front;
         for (int k = 0; k < 2; k++) {
             int kk = k < s->P.n_phases ? k : 0;
             const orc_phase* ph = &s->P.phase[kk];
@@ -538,7 +550,8 @@ static double summation_density(const orc_sim* s, int64_t i)
  * (deltaForPenalty), for phases with the penalty flag:
  *   F_p = -2 sum_w m_w/(rho_i rho_w) P n_w dx^3 |r_iw|^-2 dW/dr,
  *   P = gamma_p lambda |p_i e_iw.n_w|, lambda = (1-delta)^2/dx if delta < 1,
- *   delta = 2 |r_iw . n_w| / dx.
+ *   delta = 2 r_iw . n_w / dx (signed), r_iw = r_i - r_w,
+ * through fluid-facing wall particles only (wfront).
  * Viscosity (Morris et al. 1997):
  *   sum_j m_j (mu_i + mu_j) (r_ij . grad_i W_ij) v_ij / (rho_i rho_j (r^2 + 0.01 h^2)). */
 typedef struct { const orc_sim* s; int64_t i; const double* vel; double a[3]; } mom_ctx;
@@ -596,12 +609,12 @@ static void mom_visit_w(void* vctx, int64_t w, const double rij[3], double r)
     for (int d = 0; d < 3; d++) c->a[d] += -2.0 * m_w * pstar / (rho_i * rho_w) * gw[d];
     double zero[3] = {0.0, 0.0, 0.0};
     viscous_term(c, rij, r, rho_w, phi->mu, zero, m_w);
-    if (phi->penalty && r > 1e-6 * s->P.dp) {
+    if (phi->penalty && s->wfront[w] && r > 1e-6 * s->P.dp) {
         const double* n_w = s->nwall + 3 * w;
         double e[3] = {-rij[0] / r, -rij[1] / r, -rij[2] / r}; /* e_iw */
         double en = e[0] * n_w[0] + e[1] * n_w[1] + e[2] * n_w[2];
         double dx = s->P.dp;
-        double delta = 2.0 * r / dx * fabs(en); /* = 2 |r_iw . n_w| / dx */
+        double delta = -2.0 * r / dx * en; /* = 2 r_iw . n_w / dx, signed */
         double lambda = (delta < 1.0) ? (1.0 - delta) * (1.0 - delta) / dx : 0.0;
         double Ppen = s->P.gamma_p * lambda * fabs(p_i * en);
         double k = -2.0 * m_w / (rho_i * rho_w) * Ppen * (dx * dx * dx) / (r * r) *
@@ -765,6 +778,7 @@ orc_sim* orc_create(const orc_params* P, int64_t nf, const double* x,
     s->pw = (double*)dup(NULL, sizeof(double) * (size_t)nw);
     s->rhow = (double*)dup(NULL, sizeof(double) * 2 * (size_t)nw);
     s->nwall = (double*)dup(NULL, sizeof(double) * 3 * (size_t)nw);
+    s->wfront = (int*)calloc((size_t)(nw > 0 ? nw : 1), sizeof(int));
     s->key_f = (uint32_t*)dup(NULL, sizeof(uint32_t) * (size_t)nf);
     s->order_f = (int64_t*)dup(NULL, sizeof(int64_t) * (size_t)nf);
     s->start_f = (int64_t*)dup(NULL, sizeof(int64_t) * (size_t)(s->n_cells + 1));
@@ -797,7 +811,7 @@ void orc_destroy(orc_sim* s)
     if (!s) return;
     free(s->x); free(s->v); free(s->rho); free(s->p); free(s->a);
     free(s->drho_dt); free(s->sigma); free(s->phase);
-    free(s->xw); free(s->pw); free(s->rhow); free(s->nwall);
+    free(s->xw); free(s->pw); free(s->rhow); free(s->nwall); free(s->wfront);
     free(s->key_f); free(s->order_f); free(s->start_f);
     free(s->key_w); free(s->order_w); free(s->start_w);
     free(s);

@@ -93,7 +93,9 @@ __device__ __forceinline__ void block_add3(double* out, double a, double b, doub
 //   T_iw = K r + V v_i + kp n_w,  K = -2 m F (pi_i + pi_w)/(rho_i + rho_w),
 //   V = 2 mu_i m r^2 F / (rho_i rho_w (r^2 + eta^2)),
 //   kp = -2 m dx^3 / (rho_i rho_w) P F / r,  P = gamma_p lambda |p_i e.n|
-// (Eq. (RSatWall), Eq. (SPH_penaltyMethodTerm)), plus sigma' += W.
+// (Eq. (RSatWall), Eq. (SPH_penaltyMethodTerm); delta = 2 r.n_w/dx signed,
+// the penalty only through a fluid-facing wall particle, facing), plus
+// sigma' += W.
 // Given g = adjoint of a_i and sb = adjoint of sigma'_i, returns the
 // adjoints of r = x_i - x_w, v_i, p_i, rho_i, p_w, rho_w, mu and gamma_p.
 template <class T>
@@ -104,7 +106,8 @@ struct WallMomAdj {
 template <class T>
 __device__ __forceinline__ void wall_momentum_adj(const Cfg<T>& C, const PhaseK<T>& P, T rx, T ry, T rz, T r2,
                                                   T vx, T vy, T vz, T rho_i, T p_i, T rho_w, T p_w,
-                                                  const V4<T>& nw, T gx, T gy, T gz, T sb, WallMomAdj<T>& o)
+                                                  const V4<T>& nw, bool facing, T gx, T gy, T gz, T sb,
+                                                  WallMomAdj<T>& o)
 {
     const T rinv = p_rsqrt(r2);
     const T R = r2 * rinv;
@@ -141,9 +144,9 @@ __device__ __forceinline__ void wall_momentum_adj(const Cfg<T>& C, const PhaseK<
     o.rho_w = -pib * p_div(pi_w, rho_w) + rsb - p_div(Vb * V, rho_w);
     o.mu = Vb * T(2) * mv * Q;
     o.gp = T(0);
-    if (P.penalty && R > C.pen_rmin) {
+    if (P.penalty && R > C.pen_rmin && facing) {
         const T rn = rx * nw.x + ry * nw.y + rz * nw.z;
-        const T delta = T(2) * tabs(rn) * C.inv_dp;
+        const T delta = T(2) * rn * C.inv_dp;
         if (delta < T(1)) {
             const T en = -rn * rinv;
             const T om = T(1) - delta;
@@ -162,7 +165,7 @@ __device__ __forceinline__ void wall_momentum_adj(const Cfg<T>& C, const PhaseK<
             const T enb = Pb * C.gamma_p * lam * s * p_i;
             const T lamb = Pb * C.gamma_p * ape;
             const T deltab = lamb * (T(-2) * om * C.inv_dp);
-            const T rnb = deltab * T(2) * sgn(rn) * C.inv_dp - enb * rinv;
+            const T rnb = deltab * T(2) * C.inv_dp - enb * rinv;
             Rb += enb * rn * rinv * rinv;
             o.rx += rnb * nw.x;
             o.ry += rnb * nw.y;
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
     const V2<T>* __restrict__ wrho, const V4<T>* __restrict__ wnrm, const int4* __restrict__ wcell,
     const int32_t* __restrict__ wtag, const int32_t* __restrict__ d_tag, const V4<T>* __restrict__ pos,
     const V4<T>* __restrict__ vel, const V4<T>* __restrict__ tA, const T* __restrict__ gpw_in,
-    T* __restrict__ wc, double* gparam)
+    T* __restrict__ wc, double* gparam, int32_t* __restrict__ wfront)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int w = t / AWLP;
@@ -258,15 +261,22 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
         const bool live = wtag[w] == *d_tag;
         const V4<T> pw = wpos[w];
         const T rho_w = wrho[w].x;
+        bool facing = false;
         if (live) {
             const V4<T> nn = wnrm[w];
             const int4 c = wcell[w];
+            // the forward's fluid-facing flag, from the same scan of the same
+            // positions (k_wall_pressure), for this kernel and for the fluid side
+            scan_compact<PER, AWLP>(C, c, pw, fstart, pos, t % AWLP, [&](int, T rx, T ry, T rz, T, int) {
+                facing |= rx * nn.x + ry * nn.y + rz * nn.z < T(0);
+            });
+            facing = (__ballot_sync(group_mask<AWLP>(), facing) & group_mask<AWLP>()) != 0u;
             scan_compact<PER, AWLP>(C, c, pw, fstart, pos, t % AWLP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 // scan vector is x_w - x_f; the pair vector of the fluid is x_f - x_w
                 const V4<T> pf = pos[j], vf = vel[j], Aj = tA[j];
                 WallMomAdj<T> o;
-                wall_momentum_adj(C, P, -rx, -ry, -rz, r2, vf.x, vf.y, vf.z, vf.w, pf.w, rho_w, pw.w, nn, Aj.x,
-                                  Aj.y, Aj.z, T(0), o);
+                wall_momentum_adj(C, P, -rx, -ry, -rz, r2, vf.x, vf.y, vf.z, vf.w, pf.w, rho_w, pw.w, nn, facing,
+                                  Aj.x, Aj.y, Aj.z, T(0), o);
                 Gp += o.p_w;
                 Gr += o.rho_w;
                 den += kernel_W(C, r2 * p_rsqrt(r2));
@@ -286,6 +296,7 @@ __global__ void __launch_bounds__(LBLOCK) k_adj_wall_momentum(
                 out = pbar / den;
             }
             wc[w] = out;
+            wfront[w] = facing;
         }
     }
     block_add3(gparam, gc0, 0.0, 0.0);
@@ -311,7 +322,8 @@ __global__ void __launch_bounds__(LBLOCK, sizeof(T) == 4 ? 7 : 3) k_adj_momentum
     const T* __restrict__ drho, const int4* __restrict__ cell, const V4<T>* __restrict__ wpos,
     const V2<T>* __restrict__ wrho, const V4<T>* __restrict__ wnrm, const T* __restrict__ wc,
     const V4<T>* __restrict__ tA, const V4<T>* __restrict__ gx_in, const V4<T>* __restrict__ gv_in,
-    const V4<T>* __restrict__ geff, V4<T>* __restrict__ tX, V4<T>* __restrict__ tV, double* gparam)
+    const V4<T>* __restrict__ geff, V4<T>* __restrict__ tX, V4<T>* __restrict__ tV, double* gparam,
+    const int32_t* __restrict__ wfront)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / LP;
@@ -390,7 +402,7 @@ __global__ void __launch_bounds__(LBLOCK, sizeof(T) == 4 ? 7 : 3) k_adj_momentum
             [&](int w, const V4<T>& pw, T rx, T ry, T rz, T r2) {
                 WallMomAdj<T> o;
                 wall_momentum_adj(C, P, rx, ry, rz, r2, vi.x, vi.y, vi.z, rho_i, p_i, wrho[w].x, pw.w, wnrm[w],
-                                  Ai.x, Ai.y, Ai.z, Ai.w, o);
+                                  wfront[w] != 0, Ai.x, Ai.y, Ai.z, Ai.w, o);
                 xx += o.rx;
                 xy += o.ry;
                 xz += o.rz;

@@ -303,6 +303,7 @@ class Sim final : public SimBase {
         SPH_CUDA(cudaMemsetAsync(d_active_, 0, sizeof(unsigned long long), stream));
         SPH_CUDA(cudaMemsetAsync(d_tag_, 0, sizeof(int32_t), stream));
         SPH_CUDA(cudaMemsetAsync(wtag_, 0xff, sizeof(int32_t) * (size_t)(nw_ > 0 ? nw_ : 1), stream));
+        SPH_CUDA(cudaMemsetAsync(wfront_, 0, sizeof(int32_t) * (size_t)(nw_ > 0 ? nw_ : 1), stream));
         par_ = 0;
         if (nf_ > 0) {
             k_init_fluid<T><<<grid_for(nf_), BLOCK, 0, stream>>>(
@@ -642,7 +643,8 @@ class Sim final : public SimBase {
             if (nw_ > 0)
                 SPH_KERNEL(SPH_K_ADJ_WALL, 1,
                            k_adj_wall_momentum<T, PER><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
-                               C_, nw_, fs, WP, WR, wnrm_, wcell_, WT, TG, P0, VP, tA_, gpw_[cur], wc_, adj_param_));
+                               C_, nw_, fs, WP, WR, wnrm_, wcell_, WT, TG, P0, VP, tA_, gpw_[cur], wc_, adj_param_,
+                               wfront_));
             // The wall continuity adjoint reads only tX of the momentum
             // adjoint and writes only gpw and the parameter sums, so it runs
             // beside the fluid continuity adjoint on a side stream (not while
@@ -652,7 +654,7 @@ class Sim final : public SimBase {
                 SPH_KERNEL(SPH_K_ADJ_MOMENTUM, 1,
                            k_adj_momentum<T, PER><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                                C_, nf_, dt, 0, fs, wstart_, lf, lw, lc, P0, VP, R0, CQ, WP, WR, wnrm_, wc_, tA_,
-                               gx_[cur], gv_[cur], GE, tX_, tV_, adj_param_));
+                               gx_[cur], gv_[cur], GE, tX_, tV_, adj_param_, wfront_));
                 if (overlap) {
                     SPH_CUDA(cudaEventRecord(adj_ev_[0], stream));
                     SPH_CUDA(cudaStreamWaitEvent(adj_side_, adj_ev_[0], 0));
@@ -688,13 +690,13 @@ class Sim final : public SimBase {
             SPH_KERNEL(SPH_K_ADJ_WALL, 1,
                        k_adj_wall_momentum<T, PER><<<grid_for((int64_t)nw_ * AWLP), BLOCK, 0, stream>>>(
                            C_, nw_, fstart_, wpos_, wrho_, wnrm_, wcell_, wtag_, d_tag_, pos_[0], vel_[p0], tA_,
-                           gpw_[cur], wc_, adj_param_));
+                           gpw_[cur], wc_, adj_param_, wfront_));
         if (nf_ > 0) {
             SPH_KERNEL(SPH_K_ADJ_MOMENTUM, 1,
                        k_adj_momentum<T, PER><<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                            C_, nf_, T(0), 1, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_[p0], drho_[0],
                            cell_[p0], wpos_, wrho_, wnrm_, wc_, tA_, gx_[cur], gv_[cur], d_geff_, tX_, tV_,
-                           adj_param_));
+                           adj_param_, wfront_));
             SPH_KERNEL(SPH_K_ADJ_OTHER, 1,
                        k_adj_export<T><<<grid_for(nf_), BLOCK, 0, stream>>>(nf_, id_[p0], tX_, tV_, ox, ov, orho));
         }
@@ -1098,6 +1100,7 @@ class Sim final : public SimBase {
         if ((s = alloc(ncnt_, (size_t)LP * nf)) != SPH_OK) return s;
         nbf_live_ = nbf_;
         if ((s = alloc(wtag_, nw)) != SPH_OK) return s;
+        if ((s = alloc(wfront_, nw)) != SPH_OK) return s;
         if ((s = alloc(d_tag_, 1)) != SPH_OK) return s;
         if ((s = alloc(newcell_, nmax)) != SPH_OK) return s;
         if ((s = alloc(rank_, nmax)) != SPH_OK) return s;
@@ -1153,7 +1156,8 @@ class Sim final : public SimBase {
             // the periodic form only where an axis wraps: the others compile its code out
             auto launch = [&](auto kernel) {
                 kernel<<<grid_for((int64_t)nw_ * WLP), BLOCK, 0, stream>>>(
-                    C_, nw_, fstart_, wpos_, wcell_, pos_[0], vel_cur, wrho_, wtag_, d_tag_, d_geff_, d_active_);
+                    C_, nw_, fstart_, wpos_, wcell_, pos_[0], vel_cur, wrho_, wtag_, d_tag_, d_geff_, d_active_, wnrm_,
+                    wfront_);
             };
             SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
                        P_.periodic ? launch(k_wall_pressure<T, true>) : launch(k_wall_pressure<T, false>));
@@ -1171,7 +1175,7 @@ class Sim final : public SimBase {
             auto launch = [&](auto kernel) {
                 kernel<<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                     C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_cur, cell, phase, wpos_, wrho_, wnrm_,
-                    d_dt_, d_geff_, acc_, vel_out, sigma_, d_vmax_, d_flags_);
+                    d_dt_, d_geff_, acc_, vel_out, sigma_, d_vmax_, d_flags_, wfront_);
             };
             SPH_KERNEL(SPH_K_MOMENTUM, 1, P_.periodic ? launch(k_momentum<T, true>) : launch(k_momentum<T, false>));
         }
@@ -1559,6 +1563,7 @@ class Sim final : public SimBase {
     bool lists_current_ = false;   // the own lists hold the build of the current state
     int32_t* ncnt_ = nullptr;                  // per-lane entry counts
     int32_t *wtag_ = nullptr, *d_tag_ = nullptr;  // wall support tags, current tag
+    int32_t* wfront_ = nullptr;  // 1: fluid on the wall particle's normal side (penalty), per step
     cudaStream_t cap_stream_ = nullptr;
     // graphs keyed by (recompute without momentum, parity, reinit)
     cudaGraphExec_t gexec_[8] = {};

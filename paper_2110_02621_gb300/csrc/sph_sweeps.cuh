@@ -576,12 +576,15 @@ __device__ __forceinline__ T wall_density(const PhaseK<T>& P, const Cfg<T>& C, T
 // fluid support (not tagged by this step's neighbour build) get p_w = 0 and
 // rho_w = rho0 at once; the others split the fluid of their 27 cells over WLP
 // lanes.  rho_w = rho0 + EOS^-1(p_w) per phase, at least rho0/2.
+// The same scan marks the wall particles through which the penalty acts
+// (wfront = 1): some fluid of the support lies on the side n_w points to.
 template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
     Cfg<T> C, int32_t nw, const int32_t* __restrict__ fstart, V4<T>* __restrict__ wpos,
     const int4* __restrict__ wcell, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel,
     V2<T>* __restrict__ wrho, const int32_t* __restrict__ wtag, const int32_t* __restrict__ d_tag,
-    const V4<T>* __restrict__ geff, unsigned long long* active)
+    const V4<T>* __restrict__ geff, unsigned long long* active, const V4<T>* __restrict__ wnrm,
+    int32_t* __restrict__ wfront)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int w = t / WLP;
@@ -589,10 +592,12 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
     if (w < nw) {
         const bool multi = C.n_phases > 1;
         T num = T(0), den = T(0);
+        bool front = false;
         if (wtag[w] == *d_tag) {
             const V4<T> ge = *geff;
             const int4 c = wcell[w];
             const V4<T> pw = wpos[w];
+            const V4<T> nn = wnrm[w];
             scan_compact<PER, WLP>(C, c, pw, fstart, pos, t % WLP, [&](int j, T rx, T ry, T rz, T r2, int) {
                 const T W = kernel_W(C, r2 * p_rsqrt(r2));
                 const T p_f = reinterpret_cast<const T*>(pos + j)[3];
@@ -600,14 +605,17 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
                 const T om = multi ? p_div(W, rho_f) : W;
                 num += (p_f + rho_f * (ge.x * rx + ge.y * ry + ge.z * rz)) * om;
                 den += om;
+                front |= rx * nn.x + ry * nn.y + rz * nn.z < T(0);  // (r_f - r_w).n_w > 0
             });
             num = group_sum<WLP>(num);
             den = group_sum<WLP>(den);
+            front = (__ballot_sync(group_mask<WLP>(), front) & group_mask<WLP>()) != 0u;
         }
         if (t % WLP == 0) {
             const T p_w = den > T(0) ? num / den : T(0);
             has = den > T(0);
             reinterpret_cast<T*>(wpos + w)[3] = p_w;
+            wfront[w] = front;
             const T r0 = wall_density(C.ph[0], C, p_w);
             const T r1 = multi ? wall_density(C.ph[1], C, p_w) : r0;
             wrho[w] = V2<T>{r0, r1};
@@ -626,8 +634,10 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
 //   dU = U_L - U_R = -v_ij.r_ij/r, beta = min(3 max(dU, 0), c).
 // Plus the body force (g, or g + amp w^2 sin(w t) in a moving tank's frame),
 // the Morris viscous term, and the penalty force of
-// Eq. (SPH_penaltyMethodTerm) with delta = 2|r_iw.n_w|/dx, lambda from
-// Eq. (symbc) and dx^3 restoring its units.  Then the final kick
+// Eq. (SPH_penaltyMethodTerm) with the signed delta = 2 r_iw.n_w/dx (a
+// barrier that keeps rising behind the wall particle's plane), lambda from
+// Eq. (symbc) and dx^3 restoring its units, through the wall particles with
+// fluid on their normal's side (wfront, set by k_wall_pressure).  Then the final kick
 // v^{n+1} = v^{n+1/2} + dt/2 a^{n+1}, the number density sigma(r^{n+1}) for
 // the next reinitialisation (own phase and walls for continuity phases,
 // everything for summation phases; stored as sigma - sigma^0 from a
@@ -640,7 +650,7 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
     const int32_t* __restrict__ phase, const V4<T>* __restrict__ wpos, const V2<T>* __restrict__ wrho,
     const V4<T>* __restrict__ wnrm, const T* __restrict__ d_dt, const V4<T>* __restrict__ geff,
     V4<T>* __restrict__ acc, V4<T>* __restrict__ vel_o, T* __restrict__ dsig_o, unsigned long long* vmax_bits,
-    int32_t* flags)
+    int32_t* flags, const int32_t* __restrict__ wfront)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / LP;
@@ -701,10 +711,10 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
                         ay += kv * vi.y;
                         az += kv * vi.z;
                     }
-                    if (P.penalty && r > C.pen_rmin) {
+                    if (P.penalty && r > C.pen_rmin && wfront[w]) {
                         const V4<T> nw = wnrm[w];
                         const T rn = rx * nw.x + ry * nw.y + rz * nw.z;   // r_iw . n_w
-                        const T delta = T(2) * tabs(rn) * C.inv_dp;
+                        const T delta = T(2) * rn * C.inv_dp;              // signed
                         if (delta < T(1)) {
                             const T en = -rn * rinv;                      // e_iw . n_w
                             const T lam = (T(1) - delta) * (T(1) - delta) * C.inv_dp;

@@ -46,9 +46,30 @@ def test_penalty_is_active_in_the_adjoint_scene():
     for i in range(len(x)):
         _, ws = ref.neighbors(i)
         for w in ws:
-            rn = abs(np.dot(x[i] - xw[w], normals[w]))
+            rn = np.dot(x[i] - xw[w], normals[w])          # signed delta = 2 rn / dx
             hit += (2 * rn / sc.dp < 1.0) and np.linalg.norm(normals[w]) > 0
     assert hit > 10
+
+
+def test_torch_penalty_barrier_matches_c_oracle():
+    """A particle 0.2 dx behind a fluid-facing wall particle's plane (the C
+    oracle's pinned barrier case): the restatement's acceleration, penalty on
+    and off, equals the C oracle's."""
+    dp = 0.01
+    for penalty in (True, False):
+        sc = S.Scene(name="pen", dp=dp, h=1.3 * dp, c0=10.0, g=(0, 0, 0), lo=(-0.05, -0.05, -0.05),
+                     hi=(0.05, 0.05, 0.05), phases=[S.Phase(eos="linear", penalty=penalty)],
+                     fluid_pos=np.array([[0.0, 0.0, -0.2 * dp], [0.0, 0.0, 1.1 * dp]]),
+                     fluid_vel=np.zeros((2, 3)), fluid_phase=np.zeros(2, np.int32),
+                     wall_pos=np.array([[0.0, 0.0, 0.0], [0.0, 0.0, -dp]]), reinit_every=0)
+        rho0 = np.full(2, 1000.5)
+        ref = c_oracle(sc, rho0)
+        P = A.params_from_scene(sc, ref.wall()["normal"], ref.sigma0)
+        t = lambda a: torch.tensor(np.asarray(a, np.float64))  # noqa: E731
+        St = A.run(t(sc.fluid_pos), t(sc.fluid_vel), t(rho0), P, t(sc.c0), t(sc.gamma_p),
+                   t(sc.phases[0].mu), 0, DT)
+        a = ref.fluid()["a"]
+        assert np.allclose(St["a"].numpy(), a, rtol=1e-12, atol=1e-12 * np.abs(a).max())
 
 
 @pytest.mark.parametrize("nsteps", [0, 1, 4])

@@ -73,8 +73,20 @@ MUTANTS = [
      '(1.0 - delta) * (1.0 - delta) / dx',
      '(1.0 - delta) / dx'),
     ('penalty delta factor',
-     'double delta = 2.0 * r / dx * fabs(en);',
-     'double delta = r / dx * fabs(en);'),
+     'double delta = -2.0 * r / dx * en;',
+     'double delta = -1.0 * r / dx * en;'),
+    ('penalty delta unsigned',
+     'double delta = -2.0 * r / dx * en;',
+     'double delta = 2.0 * r / dx * fabs(en);'),
+    ('penalty delta sign',
+     'double delta = -2.0 * r / dx * en;',
+     'double delta = 2.0 * r / dx * en;'),
+    ('penalty fluid-facing side',
+     'if (rwf[0] * n[0] + rwf[1] * n[1] + rwf[2] * n[2] < 0.0) c->front = 1;',
+     'if (rwf[0] * n[0] + rwf[1] * n[1] + rwf[2] * n[2] > 0.0) c->front = 1;'),
+    ('penalty fluid-facing ignored',
+     'if (phi->penalty && s->wfront[w] && r > 1e-6 * s->P.dp) {',
+     'if (phi->penalty && r > 1e-6 * s->P.dp) {'),
     ('viscosity eta',
      '(r * r + 0.01 * s->P.h * s->P.h)',
      '(r * r + 0.1 * s->P.h * s->P.h)'),
@@ -264,8 +276,14 @@ ADJOINT_MUTANTS = [
      'lam = torch.where(act, (1.0 - delta) ** 2 / dx, torch.zeros_like(delta))',
      'lam = torch.where(act, (1.0 - delta) / dx, torch.zeros_like(delta))'),
     ('penalty delta factor',
-     'delta = 2.0 * r / dx * torch.abs(en)',
-     'delta = r / dx * torch.abs(en)'),
+     'delta = 2.0 * rn / dx',
+     'delta = rn / dx'),
+    ('penalty delta unsigned',
+     'delta = 2.0 * rn / dx',
+     'delta = 2.0 * torch.abs(rn) / dx'),
+    ('penalty fluid-facing ignored',
+     'act = facing[ww] & (delta < 1.0) & (r > 1e-6 * dx)',
+     'act = (delta < 1.0) & (r > 1e-6 * dx)'),
     ('reinit factor',
      'return rho_num + torch.clamp(rho - rho_num, min=0.0) * P.rho0 / rho',
      'return rho_num + torch.clamp(rho - rho_num, min=0.0)'),

@@ -512,6 +512,58 @@ def test_penalty_hand_computed_pair():
     assert np.all(on3 == off3)
 
 
+def _penalty_pair_expect(z_i, rho, dp=0.01, h=0.013):
+    """F_p of Eq. (SPH_penaltyMethodTerm) on a particle at height z_i above a
+    wall particle with n_w = +z (delta = 2 z_i / dx signed), equal fluid and
+    wall densities, p = c0^2 (rho - rho0) with c0 = 10; dW/dr by central
+    difference of W."""
+    p_i = 100.0 * (rho - 1000.0)
+    m = 1000.0 * dp ** 3
+    delta = 2 * z_i / dp
+    lam = (1 - delta) ** 2 / dp if delta < 1 else 0.0
+    r = abs(z_i)
+    P = lam * abs(p_i)                    # |e_iw . n_w| = 1 on the axis
+    e = 1e-7 * h
+    dWdr = (oracle.W(r + e, h) - oracle.W(r - e, h)) / (2 * e)
+    return -2 * m / (rho * rho) * P * dp ** 3 / r ** 2 * dWdr
+
+
+def test_penalty_barrier_behind_the_plane():
+    """A particle 0.2 dx behind the upper wall particle's plane (between the
+    two wall layers), with a second particle 1.1 dx in front making the upper
+    wall particle fluid-facing: delta = -0.4 (signed), lambda = 1.4^2 / dx,
+    and F_p pushes the particle back along n_w = +z.  Under |delta| it would
+    be 0.36 / dx.  The particle in front (delta = 2.2) and the lower wall
+    particle (normal away from both) add nothing."""
+    dp, rho = 0.01, 1000.5
+    sc = _penalty_scene(-0.2 * dp)
+    sc.fluid_pos = np.array([[0.0, 0.0, -0.2 * dp], [0.0, 0.0, 1.1 * dp]])
+    sc.fluid_vel = np.zeros((2, 3))
+    sc.fluid_phase = np.zeros(2, np.int32)
+    r2 = np.full(2, rho)
+    on = oracle.OracleSim(sc, rho=r2).fluid()["a"]
+    sc.phases[0].penalty = False
+    off = oracle.OracleSim(sc, rho=r2).fluid()["a"]
+    Fp = on - off
+    assert Fp[0, 0] == 0.0 and Fp[0, 1] == 0.0
+    assert Fp[0, 2] > 0
+    assert Fp[0, 2] == pytest.approx(_penalty_pair_expect(-0.2 * dp, rho), rel=1e-7)
+    assert np.all(Fp[1] == 0.0)
+
+
+def test_penalty_only_through_fluid_facing_wall_particles():
+    """The same penetrated particle alone: no fluid lies on the side of the
+    upper wall particle's normal, so that particle is not fluid-facing and
+    the penalty is silent (as it is for the outer wall layers, whose normals
+    point away from the fluid)."""
+    dp, rho = 0.01, 1000.5
+    sc = _penalty_scene(-0.2 * dp)
+    on = oracle.OracleSim(sc, rho=np.array([rho])).fluid()["a"][0]
+    sc.phases[0].penalty = False
+    off = oracle.OracleSim(sc, rho=np.array([rho])).fluid()["a"][0]
+    assert np.all(on == off)
+
+
 def test_penalty_silent_at_rest():
     """In a lattice tank at rest every fluid particle is at least dx from the
     tangent plane of each wall neighbour: switching the penalty on changes
