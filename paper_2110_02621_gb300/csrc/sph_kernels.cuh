@@ -132,7 +132,16 @@ __global__ void k_predict(Cfg<T> C, int32_t n, const V4<T>* __restrict__ pos, co
     kick_drift<T, KAHAN>(C, dt, p, v, a, cm, c);
     uint32_t key = cell_key(C, c.x, c.y, c.z);
     int bucket = key == KEY_NONE ? C.n_cells : (int)key;
-    rank[s] = atomicAdd(counts + bucket, 1);
+    // Consecutive particles mostly share a cell: the lanes of a warp with the
+    // same bucket take one atomic (their leader adds their number) and each
+    // its rank among them.  The arrival order is irrelevant: the gather
+    // orders every cell by id.
+    const unsigned peers = __match_any_sync(__activemask(), bucket);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counts + bucket, __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    rank[s] = base + __popc(peers & ((1u << lane) - 1u));
     c.w = (int)key;
     newcell[s] = c;
 }

@@ -387,12 +387,40 @@ class Sim final : public SimBase {
         if (s0 != SPH_OK) return s0;
         for (int32_t k = 0; k < nsteps; ++k) {
             bool reinit = P_.reinit_every > 0 && (steps_ % P_.reinit_every) == 0;
+            const bool sig = sigma_next();
             // the kernel sequence of a step as one CUDA graph launch, unless
             // kernels are being timed one by one
-            sph_status s = prof_mask_ ? one_step(reinit) : graph_step(reinit);
+            sph_status s = prof_mask_ ? one_step(reinit, true, sig) : graph_step(reinit, true, sig);
             if (s != SPH_OK) return s;
             ++steps_;
         }
+        return SPH_OK;
+    }
+
+    // Whether the step about to run must leave sigma(r^{n+1}) for the next
+    // one: only when that step reinitialises (the other readers, the state
+    // export and sph_reinit_density, call ensure_sigma).
+    bool sigma_next() const
+    {
+        return P_.reinit_every > 0 && ((steps_ + 1) % P_.reinit_every) == 0;
+    }
+
+    // sigma - sigma^0 at the current positions, when the last momentum sweep
+    // left it out (k_sigma: the same bits the sweep would have written).
+    sph_status ensure_sigma()
+    {
+        if (sigma_valid_ || nf_ == 0) return SPH_OK;
+        if (!lists_current_) {
+            sph_status s = neighbors(pos_[0], cell_[par_]);
+            if (s != SPH_OK) return s;
+        }
+        auto launch = [&](auto kernel) {
+            kernel<<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_,
+                                                                      pos_[0], cell_[par_], phase_[par_], wpos_,
+                                                                      sigma_);
+        };
+        SPH_KERNEL(SPH_K_OTHER, 1, P_.periodic ? launch(k_sigma<T, true>) : launch(k_sigma<T, false>));
+        sigma_valid_ = true;
         return SPH_OK;
     }
 
@@ -446,6 +474,7 @@ class Sim final : public SimBase {
 
     sph_status reinit() override
     {
+        if (sph_status s = ensure_sigma(); s != SPH_OK) return s;
         if (nf_ > 0)
             SPH_KERNEL(SPH_K_OTHER, 1,
                        k_reinit<T><<<grid_for(nf_), BLOCK, 0, stream>>>(C_, nf_, sigma_, cell_[par_], phase_[par_],
@@ -526,13 +555,13 @@ class Sim final : public SimBase {
                 nbf_ = f->nbf;
                 nbw_ = f->nbw;
                 ncnt_ = f->ncnt;
-                s = one_step(c.reinit);
+                s = one_step(c.reinit, true, sigma_next());
                 nbf_ = lf;
                 nbw_ = lw;
                 ncnt_ = lc;
                 if (s == SPH_OK) s = keep_products(*f, c.par);
             } else {
-                s = prof_mask_ ? one_step(c.reinit) : graph_step(c.reinit);
+                s = prof_mask_ ? one_step(c.reinit, true, sigma_next()) : graph_step(c.reinit, true, sigma_next());
             }
             if (s != SPH_OK) return s;
             // the dt the step used, kept on the device for the recompute
@@ -742,6 +771,8 @@ class Sim final : public SimBase {
 
     sph_status get_state(const sph_state_out& o, int32_t where) override
     {
+        if (o.sigma)
+            if (sph_status s = ensure_sigma(); s != SPH_OK) return s;
         const bool host = where == SPH_HOST;
         const size_t n1 = sizeof(double) * (size_t)nf_, n3 = 3 * n1;
         const size_t w1 = sizeof(double) * (size_t)nw_;
@@ -1156,8 +1187,7 @@ class Sim final : public SimBase {
             // the periodic form only where an axis wraps: the others compile its code out
             auto launch = [&](auto kernel) {
                 kernel<<<grid_for((int64_t)nw_ * WLP), BLOCK, 0, stream>>>(
-                    C_, nw_, fstart_, wpos_, wcell_, pos_[0], vel_cur, wrho_, wtag_, d_tag_, d_geff_, d_active_, wnrm_,
-                    wfront_);
+                    C_, nw_, fstart_, wpos_, wcell_, pos_[0], vel_cur, wrho_, wtag_, d_tag_, d_geff_, d_active_, wnrm_);
             };
             SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
                        P_.periodic ? launch(k_wall_pressure<T, true>) : launch(k_wall_pressure<T, false>));
@@ -1167,7 +1197,8 @@ class Sim final : public SimBase {
 
     // momentum from pos[0] / vel_cur; writes acc, vel_out (final kick),
     // sigma - sigma^0 and U_max
-    sph_status momentum(const V4<T>* vel_cur, V4<T>* vel_out, const int4* cell, const int32_t* phase)
+    sph_status momentum(const V4<T>* vel_cur, V4<T>* vel_out, const int4* cell, const int32_t* phase,
+                        bool sigma = true)
     {
         if (nf_ == 0) return SPH_OK;
         {
@@ -1175,9 +1206,15 @@ class Sim final : public SimBase {
             auto launch = [&](auto kernel) {
                 kernel<<<grid_for((int64_t)nf_ * LP), BLOCK, 0, stream>>>(
                     C_, nf_, fstart_, wstart_, nbf_, nbw_, ncnt_, pos_[0], vel_cur, cell, phase, wpos_, wrho_, wnrm_,
-                    d_dt_, d_geff_, acc_, vel_out, sigma_, d_vmax_, d_flags_, wfront_);
+                    d_dt_, d_geff_, acc_, vel_out, sigma_, d_vmax_, d_flags_);
             };
-            SPH_KERNEL(SPH_K_MOMENTUM, 1, P_.periodic ? launch(k_momentum<T, true>) : launch(k_momentum<T, false>));
+            if (sigma)
+                SPH_KERNEL(SPH_K_MOMENTUM, 1,
+                           P_.periodic ? launch(k_momentum<T, true, true>) : launch(k_momentum<T, false, true>));
+            else
+                SPH_KERNEL(SPH_K_MOMENTUM, 1,
+                           P_.periodic ? launch(k_momentum<T, true, false>) : launch(k_momentum<T, false, false>));
+            sigma_valid_ = sigma;
         }
         return SPH_OK;
     }
@@ -1188,7 +1225,7 @@ class Sim final : public SimBase {
     //   continuity: pos[1], vel[q], drho[1] -> pos[0], vel[p], drho[0], acc.w
     //   wall pressure, momentum read pos[0], vel[p]; momentum writes vel[q]
     // so pos and drho stay in [0] while vel, comp, cell, id, phase alternate.
-    sph_status one_step(bool reinit, bool with_momentum = true)
+    sph_status one_step(bool reinit, bool with_momentum = true, bool sigma = true)
     {
         const int p = par_, q = par_ ^ 1;
         // the step's dt and wall tag come from k_predict, the U_max reset from
@@ -1230,7 +1267,7 @@ class Sim final : public SimBase {
         sph_status s = wall_pressure(vel_[p]);
         if (s != SPH_OK) return s;
         if (with_momentum) {
-            s = momentum(vel_[p], vel_[q], cell_[q], phase_[q]);
+            s = momentum(vel_[p], vel_[q], cell_[q], phase_[q], sigma);
             if (s != SPH_OK) return s;
         }
         par_ = q;
@@ -1242,9 +1279,9 @@ class Sim final : public SimBase {
     // kernel argument, so up to four graphs exist, captured on first use on
     // an internal stream (the caller's may be the legacy default stream,
     // which cannot be captured) and launched on the caller's stream.
-    sph_status graph_step(bool reinit, bool with_momentum = true)
+    sph_status graph_step(bool reinit, bool with_momentum = true, bool sigma = true)
     {
-        const int key = (with_momentum ? 0 : 4) | (par_ << 1) | (reinit ? 1 : 0);
+        const int key = (sigma ? 8 : 0) | (with_momentum ? 0 : 4) | (par_ << 1) | (reinit ? 1 : 0);
         if (!gexec_[key]) {
             if (!cap_stream_) SPH_CUDA(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking));
             cudaStream_t user = stream;
@@ -1253,7 +1290,7 @@ class Sim final : public SimBase {
             memcpy(before, launches_, sizeof before);
             stream = cap_stream_;
             cudaError_t e = cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal);
-            sph_status s = e == cudaSuccess ? one_step(reinit, with_momentum) : SPH_OK;
+            sph_status s = e == cudaSuccess ? one_step(reinit, with_momentum, sigma) : SPH_OK;
             cudaGraph_t g = nullptr;
             cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap_stream_, &g) : e;
             stream = user;
@@ -1272,6 +1309,7 @@ class Sim final : public SimBase {
             SPH_CUDA(e);
         }
         SPH_CUDA(cudaGraphLaunch(gexec_[key], stream));
+        if (with_momentum) sigma_valid_ = sigma;
         for (int k = 0; k < SPH_NK; ++k) launches_[k] += glaunch_[key][k];
         par_ ^= 1;
         return SPH_OK;
@@ -1292,6 +1330,7 @@ class Sim final : public SimBase {
         int64_t steps = 0;
         T dt = T(0);
         bool reinit = false;
+        bool sigma_valid = false;
     };
 
     sph_status save(Ckpt& c)
@@ -1335,6 +1374,7 @@ class Sim final : public SimBase {
         }
         c.par = par_;
         c.steps = steps_;
+        c.sigma_valid = sigma_valid_;
         return copy_ckpt(c, true);
     }
 
@@ -1489,6 +1529,7 @@ class Sim final : public SimBase {
         if (s != SPH_OK) return s;
         par_ = c.par;
         steps_ = c.steps;
+        sigma_valid_ = c.sigma_valid;
         return SPH_OK;
     }
 
@@ -1563,11 +1604,12 @@ class Sim final : public SimBase {
     bool lists_current_ = false;   // the own lists hold the build of the current state
     int32_t* ncnt_ = nullptr;                  // per-lane entry counts
     int32_t *wtag_ = nullptr, *d_tag_ = nullptr;  // wall support tags, current tag
-    int32_t* wfront_ = nullptr;  // 1: fluid on the wall particle's normal side (penalty), per step
+    int32_t* wfront_ = nullptr;  // the adjoint's fluid-facing flags of the step it reverses
     cudaStream_t cap_stream_ = nullptr;
     // graphs keyed by (recompute without momentum, parity, reinit)
-    cudaGraphExec_t gexec_[8] = {};
-    int64_t glaunch_[8][SPH_NK] = {};
+    cudaGraphExec_t gexec_[16] = {};
+    int64_t glaunch_[16][SPH_NK] = {};
+    bool sigma_valid_ = false;  // sigma_ holds sigma - sigma^0 of the current positions
     int4* newcell_ = nullptr;
     int32_t *rank_ = nullptr, *tmp_src_ = nullptr, *tmp_id_ = nullptr;
     int32_t *counts_ = nullptr, *fstart_ = nullptr, *wstart_ = nullptr, *sums_ = nullptr;

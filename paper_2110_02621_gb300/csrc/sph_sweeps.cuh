@@ -55,12 +55,15 @@ __device__ __forceinline__ T dist2(T x, T y, T z)
 
 // Kahan-compensated accumulation; the sum is s - c.  Used for number
 // densities, whose deviation from the lattice value is the signal.
+// Every operation rounds on its own (the _rn intrinsics are never fused with
+// the product that made x), so the sum has the same bits in every kernel that
+// adds the same terms in the same order.
 template <class T>
 __device__ __forceinline__ void kahan_add(T& s, T& c, T x)
 {
-    const T y = x - c;
-    const T t = s + y;
-    c = (t - s) - y;
+    const T y = sub_rn(x, c);
+    const T t = add_rn(s, y);
+    c = sub_rn(sub_rn(t, s), y);
     s = t;
 }
 
@@ -577,14 +580,14 @@ __device__ __forceinline__ T wall_density(const PhaseK<T>& P, const Cfg<T>& C, T
 // rho_w = rho0 at once; the others split the fluid of their 27 cells over WLP
 // lanes.  rho_w = rho0 + EOS^-1(p_w) per phase, at least rho0/2.
 // The same scan marks the wall particles through which the penalty acts
-// (wfront = 1): some fluid of the support lies on the side n_w points to.
+// (wnrm.w = 1, else 0): some fluid of the support lies on the side n_w
+// points to.
 template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
     Cfg<T> C, int32_t nw, const int32_t* __restrict__ fstart, V4<T>* __restrict__ wpos,
     const int4* __restrict__ wcell, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel,
     V2<T>* __restrict__ wrho, const int32_t* __restrict__ wtag, const int32_t* __restrict__ d_tag,
-    const V4<T>* __restrict__ geff, unsigned long long* active, const V4<T>* __restrict__ wnrm,
-    int32_t* __restrict__ wfront)
+    const V4<T>* __restrict__ geff, unsigned long long* active, V4<T>* __restrict__ wnrm)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int w = t / WLP;
@@ -615,7 +618,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
             const T p_w = den > T(0) ? num / den : T(0);
             has = den > T(0);
             reinterpret_cast<T*>(wpos + w)[3] = p_w;
-            wfront[w] = front;
+            reinterpret_cast<T*>(wnrm + w)[3] = front ? T(1) : T(0);
             const T r0 = wall_density(C.ph[0], C, p_w);
             const T r1 = multi ? wall_density(C.ph[1], C, p_w) : r0;
             wrho[w] = V2<T>{r0, r1};
@@ -637,12 +640,15 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
 // Eq. (SPH_penaltyMethodTerm) with the signed delta = 2 r_iw.n_w/dx (a
 // barrier that keeps rising behind the wall particle's plane), lambda from
 // Eq. (symbc) and dx^3 restoring its units, through the wall particles with
-// fluid on their normal's side (wfront, set by k_wall_pressure).  Then the final kick
+// fluid on their normal's side (wnrm.w, set by k_wall_pressure).  Then the final kick
 // v^{n+1} = v^{n+1/2} + dt/2 a^{n+1}, the number density sigma(r^{n+1}) for
 // the next reinitialisation (own phase and walls for continuity phases,
 // everything for summation phases; stored as sigma - sigma^0 from a
 // compensated sum) and U_max for the next dt.
-template <class T, bool PER>
+// SIG = false leaves sigma out (and dsig_o untouched): the number density is
+// read only by the next step's reinitialisation, so steps before a step
+// without one skip it (k_sigma gives it on demand, bit for bit the same).
+template <class T, bool PER, bool SIG = true>
 __global__ void __launch_bounds__(LBLOCK) k_momentum(
     Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
     const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw, const int32_t* __restrict__ cnt,
@@ -650,7 +656,7 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
     const int32_t* __restrict__ phase, const V4<T>* __restrict__ wpos, const V2<T>* __restrict__ wrho,
     const V4<T>* __restrict__ wnrm, const T* __restrict__ d_dt, const V4<T>* __restrict__ geff,
     V4<T>* __restrict__ acc, V4<T>* __restrict__ vel_o, T* __restrict__ dsig_o, unsigned long long* vmax_bits,
-    int32_t* flags, const int32_t* __restrict__ wfront)
+    int32_t* flags)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = t / LP;
@@ -691,7 +697,7 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
                     ax += k * rx;
                     ay += k * ry;
                     az += k * rz;
-                    if (sig_all || phj == ph) kahan_add(sg, se, W);
+                    if (SIG && (sig_all || phj == ph)) kahan_add(sg, se, W);
                 };
             auto wall_pair = [&](int w, const V4<T>& pw, T rx, T ry, T rz, T r2) {
                     const V2<T> rw = wrho[w];
@@ -711,11 +717,11 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
                         ay += kv * vi.y;
                         az += kv * vi.z;
                     }
-                    if (P.penalty && r > C.pen_rmin && wfront[w]) {
+                    if (P.penalty && r > C.pen_rmin) {
                         const V4<T> nw = wnrm[w];
                         const T rn = rx * nw.x + ry * nw.y + rz * nw.z;   // r_iw . n_w
                         const T delta = T(2) * rn * C.inv_dp;              // signed
-                        if (delta < T(1)) {
+                        if (delta < T(1) && nw.w != T(0)) {
                             const T en = -rn * rinv;                      // e_iw . n_w
                             const T lam = (T(1) - delta) * (T(1) - delta) * C.inv_dp;
                             const T Ppen = C.gamma_p * lam * tabs(p_i * en);
@@ -725,21 +731,21 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
                             az += kp * nw.z;
                         }
                     }
-                    kahan_add(sg, se, W);
+                    if (SIG) kahan_add(sg, se, W);
                 };
             for_neighbors<PER>(C, n, t, pi, c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos, fluid_pair, wall_pair);
             const V4<T> ge = *geff;
             ax = group_sum(ax) + ge.x;
             ay = group_sum(ay) + ge.y;
             az = group_sum(az) + ge.z;
-            group_kahan(sg, se);
+            if (SIG) group_kahan(sg, se);
             const V4<T> vo{fma_rn(hdt, ax, vi.x), fma_rn(hdt, ay, vi.y), fma_rn(hdt, az, vi.z), rho_i};
             bad = !(f_finite(ax) && f_finite(ay) && f_finite(az));
             speed = f_sqrt(vo.x * vo.x + vo.y * vo.y + vo.z * vo.z);
             if (lead) {
                 acc[i] = V4<T>{ax, ay, az, acc[i].w};
                 vel_o[i] = vo;
-                dsig_o[i] = minus_ref(sg, se, C.sigma0_hi, C.sigma0_lo);
+                if (SIG) dsig_o[i] = minus_ref(sg, se, C.sigma0_hi, C.sigma0_lo);
             }
         }
     }
@@ -759,6 +765,50 @@ __global__ void __launch_bounds__(LBLOCK) k_momentum(
         if (m) atomicMax(vmax_bits, m);
         if (nbad) atomicOr(flags, 1);
     }
+}
+
+// sigma - sigma^0 of every particle at the positions of the current lists,
+// for steps whose momentum sweep left it out: the same lanes, list walk,
+// kernel values (kernel_WF), compensated sums and shuffle tree as
+// k_momentum with SIG, so the result is the same bits.  Particles outside
+// the grid get 0, as from k_continuity.
+template <class T, bool PER>
+__global__ void __launch_bounds__(LBLOCK) k_sigma(
+    Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
+    const int32_t* __restrict__ nbf, const int32_t* __restrict__ nbw, const int32_t* __restrict__ cnt,
+    const V4<T>* __restrict__ pos, const int4* __restrict__ cell, const int32_t* __restrict__ phase,
+    const V4<T>* __restrict__ wpos, T* __restrict__ dsig_o)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = t / LP;
+    const bool lead = (t % LP) == 0;
+    if (i >= n) return;
+    const int4 c = cell[i];
+    if (c.w < 0) {
+        if (lead) dsig_o[i] = T(0);
+        return;
+    }
+    const int ph = phase[i];
+    const bool multi = C.n_phases > 1;
+    const bool sig_all = C.ph[ph].density == 1;
+    T sg = lead ? C.W0 : T(0), se = T(0);
+    for_neighbors<PER>(
+        C, n, t, pos[i], c, nbf, nbw, cnt[t], fstart, wstart, pos, wpos,
+        [&](int j, const V4<T>&, T, T, T, T r2) {
+            const T r = r2 * p_rsqrt(r2);
+            T W, F;
+            kernel_WF(C, r, W, F);
+            const int phj = multi ? phase[j] : 0;
+            if (sig_all || phj == ph) kahan_add(sg, se, W);
+        },
+        [&](int, const V4<T>&, T, T, T, T r2) {
+            const T r = r2 * p_rsqrt(r2);
+            T W, F;
+            kernel_WF(C, r, W, F);
+            kahan_add(sg, se, W);
+        });
+    group_kahan(sg, se);
+    if (lead) dsig_o[i] = minus_ref(sg, se, C.sigma0_hi, C.sigma0_lo);
 }
 
 }  // namespace sph
