@@ -691,6 +691,8 @@ def adjoint_block(stream, reps: int = 3):
             "forward_ms": fwd, "tape_ms": tape_ms, "backward_ms": bwd_ms,
             "fwd_bwd_over_fwd": (tape_ms + bwd_ms) / fwd,
             "timing": "host wall clock around the calls (each synchronises), best of 3",
+            "covers": "one phase with continuity density (two-phase and summation-density runs return "
+                      "SPH_ERR_UNSUPPORTED); the penalty is silent in this run from rest, so dL/dgamma_p is 0",
             "kernel_ms": kernel_ms,
             "fp32_vs_fp64_grad_rel_err": {k: rel(g32[k], g64[k]) for k in ("x", "v", "rho")},
             "fp32_vs_fp64_param_grad": {k: [g32[k], g64[k]] for k in ("c0", "gamma_p", "mu")}}

@@ -332,8 +332,63 @@ __global__ void k_wall_rows(Cfg<T> C, int32_t n_cells, const int32_t* __restrict
 }
 
 // --------------------------------------------------------- neighbour lists
-// Ten blocks per SM (48 registers, no spills): measured 64.3 against 65.7 us
-// at 80 k particles and 5.33 against 5.66 ms at 10.35 M without the bound.
+// Evens out the LP sub-lists of one particle.  The build gives lane l every
+// LP-th candidate, so the lanes' hit counts c_l scatter around N/LP, and a
+// sweep's warp walks as many entries as its longest sub-list.  Here lane l
+// keeps q_l = (N + LP - 1 - l) / LP entries: each lane with c_l > q_l moves
+// its last c_l - q_l entries to the ends of the short sub-lists (excess and
+// room both ranked in lane order, so the moves are fixed).  Entries stay
+// what they were, only their lane changes.  A particle whose sub-list
+// overflowed (some c_l > CAP, entries missing) keeps its counts: its sweeps
+// fall back to the cell scan, whose lane shares are the build's.  col points
+// at lane 0's column of the particle (entry k of lane l at k stride + l).
+// Called by all LP lanes of the group; returns lane l's count.
+template <int CAP>
+__device__ __forceinline__ int balance_lists(int32_t* __restrict__ col, uint32_t stride, int l, int cnt)
+{
+    const unsigned m = group_mask<LP>();
+    int c[LP], q[LP];
+    int N = 0;
+    bool over = false;
+#pragma unroll
+    for (int k = 0; k < LP; ++k) {
+        c[k] = __shfl_sync(m, cnt, k, LP);
+        N += c[k];
+        over |= c[k] > CAP;
+    }
+    if (over) return cnt;
+    int before = 0;  // excess of the lanes before l
+#pragma unroll
+    for (int k = 0; k < LP; ++k) {
+        q[k] = (N + LP - 1 - k) / LP;
+        if (k < l) before += c[k] > q[k] ? c[k] - q[k] : 0;
+    }
+    const int ql = (N + LP - 1 - l) / LP;  // q[l], c[l] = cnt (no indexed access)
+    // four entries at a time: their loads are issued before any store
+    constexpr int CH = 4;
+    for (int r0 = 0; r0 < cnt - ql; r0 += CH) {
+        int32_t e[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (r0 + u < cnt - ql) e[u] = col[(size_t)(uint32_t)(ql + r0 + u) * stride + l];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            if (r0 + u >= cnt - ql) break;
+            const int g = before + r0 + u;  // rank of this entry among all moved ones
+            int acc = 0;
+#pragma unroll
+            for (int d = 0; d < LP; ++d) {
+                const int room = q[d] > c[d] ? q[d] - c[d] : 0;
+                if (g >= acc && g < acc + room) col[(size_t)(uint32_t)(c[d] + g - acc) * stride + d] = e[u];
+                acc += room;
+            }
+        }
+    }
+    return ql;
+}
+
+// Ten blocks per SM (48 registers): measured 64.3 against 65.7 us at 80 k
+// particles and 5.33 against 5.66 ms at 10.35 M without the bound.
 template <class T, bool PER>
 __global__ void __launch_bounds__(LBLOCK, 10) k_neighbors(
     Cfg<T> C, int32_t n, const int32_t* __restrict__ fstart, const int32_t* __restrict__ wstart,
@@ -368,6 +423,8 @@ __global__ void __launch_bounds__(LBLOCK, 10) k_neighbors(
                     nw += hit;
                 },
                 wr);
+        nf = balance_lists<SUBF>(nbf + (size_t)LP * i, stride, l, nf);
+        nw = balance_lists<SUBW>(nbw + (size_t)LP * i, stride, l, nw);
     }
     cnt[t] = nf | (nw << 16);
 }
