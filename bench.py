@@ -281,9 +281,19 @@ def kernel_work(kind: str, n_fluid: int, ff: float, fw: float, active: float, n_
     return "hbm", n_fluid * BYTES_PER_PARTICLE[kind]
 
 
-def kernel_roofline(kind: str, ms: float, work, peaks: dict) -> dict:
+# fluid particles of the workload the committed ncu capture was taken on
+# (the 80,400-particle dam break); other workloads scale its per-launch
+# counters by their particle count
+NCU_CAPTURE_N_FLUID = 80400
+
+
+def kernel_roofline(kind: str, ms: float, work, peaks: dict, n_fluid: int = NCU_CAPTURE_N_FLUID) -> dict:
     """achieved = algorithmic work per launch / launch time, against the FP32
-    FMA peak (pair sweeps) or the measured copy bandwidth (the rest)."""
+    FMA peak (pair sweeps) or the measured copy bandwidth (the rest).  The
+    DRAM traffic and warp instructions come from the committed ncu capture;
+    for a workload of another size they are that capture's figures scaled by
+    n_fluid / NCU_CAPTURE_N_FLUID (per-particle work of the same kind)."""
+    scale = n_fluid / NCU_CAPTURE_N_FLUID
     bound, amount = work
     if bound == "alu":
         ach = amount / (ms / 1e3) / 1e12
@@ -296,16 +306,23 @@ def kernel_roofline(kind: str, ms: float, work, peaks: dict) -> dict:
         r = {"bound": "hbm", "kernel": f"k_{kind}", "achieved": ach, "peak": peaks["hbm_gbs"],
              "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "bytes_per_launch": amount,
              "peak_source": peaks["hbm_source"]}
-    r["traffic"] = ncu_traffic(f"k_{kind}")
+    traffic = ncu_traffic(f"k_{kind}")
+    r["traffic"] = None if traffic is None else traffic * scale
+    if traffic is not None and scale != 1.0:
+        r["traffic_source"] = (f"ncu capture of the {NCU_CAPTURE_N_FLUID}-particle dam break, scaled by "
+                               f"{n_fluid}/{NCU_CAPTURE_N_FLUID} particles")
     r["ms_per_launch"] = ms
     # the same launch against the SMs' instruction issue rate, from ncu's
     # warp-instruction count of the committed capture (current sources only)
     inst = ncu_traffic(f"k_{kind}", "warp_inst_per_launch")
     if inst:
+        inst = inst * scale
         issue = inst / (ms / 1e3) / 1e12
+        src = "smsp__inst_executed.sum of the committed ncu capture"
+        if scale != 1.0:
+            src += f", scaled by {n_fluid}/{NCU_CAPTURE_N_FLUID} particles"
         r["issue"] = {"achieved": issue, "peak": peaks["issue_twips"], "unit": "T warp-instructions/s",
-                      "frac": issue / peaks["issue_twips"], "warp_inst_per_launch": inst,
-                      "source": "smsp__inst_executed.sum of the committed ncu capture"}
+                      "frac": issue / peaks["issue_twips"], "warp_inst_per_launch": inst, "source": src}
     return r
 
 
@@ -511,7 +528,8 @@ def run_gpu(args):
     pairs_fw = 0.5 * (fw0 + fw1)
     peaks = device_peaks()
     roofline = kernel_roofline(dominant, dom_ms,
-                               kernel_work(dominant, sc.n_fluid, pairs_ff, pairs_fw, active_mean, n_cells), peaks)
+                               kernel_work(dominant, sc.n_fluid, pairs_ff, pairs_fw, active_mean, n_cells), peaks,
+                               sc.n_fluid)
     t_step = t_ms / args.steps * 1e3
     step_roof = step_roofline(sc.n_fluid, pairs_ff, pairs_fw, t_step, peaks)
     step_roof_design = step_roofline_design(sc.n_fluid, pairs_ff, pairs_fw, active_mean, n_cells, cand_tests,
@@ -764,7 +782,8 @@ def other_workloads(stream, flush, steps: int = 50, fp64_steps: int = 20):
                          "dtype": "f32", "kernel_us_per_step": kus,
                          "pairs_per_fluid_particle": {"fluid": ff / sc.n_fluid, "wall": fw / sc.n_fluid},
                          "roofline": kernel_roofline(dom, kus[dom] / 1e3,
-                                                     kernel_work(dom, sc.n_fluid, ff, fw, active, n_cells), peaks),
+                                                     kernel_work(dom, sc.n_fluid, ff, fw, active, n_cells), peaks,
+                                                     sc.n_fluid),
                          "step_roofline": step_roofline(sc.n_fluid, ff, fw, t_step, peaks),
                          "streaming_roofline": streaming_roofline(kus, sc.n_fluid, n_cells, peaks["hbm_gbs"]),
                          "fp64_plain": {"ms_per_step": t64 / fp64_steps, "steps": fp64_steps, "dtype": "f64",
