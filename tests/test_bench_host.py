@@ -102,3 +102,21 @@ def test_roofline_accounting_follows_the_algorithmic_work():
     assert s["flops"] == want_flops and s["bytes"] == 300 * n
     t = max(want_flops / (peaks["fp32_tflops"] * 1e12), 300 * n / (6780e9)) * 1e6
     assert abs(s["frac"] - t / 150.0) < 1e-12
+
+
+def test_ncu_counters_scale_with_the_workload(monkeypatch):
+    """The committed capture is of the 80,400-particle dam break: a line for
+    another workload takes its per-launch DRAM bytes and warp instructions
+    scaled by the particle count and says so; the capture's own workload takes
+    them as recorded."""
+    import bench
+    rec = {"dram_bytes_per_launch": 1000, "warp_inst_per_launch": 5000.0}
+    monkeypatch.setattr(bench, "ncu_traffic", lambda kernel, field="dram_bytes_per_launch": rec[field])
+    peaks = {"sm_count": 152, "sm_max_mhz": 2070.0, "fp32_tflops": 80.5, "issue_twips": 1.25856,
+             "hbm_gbs": 6780.0, "hbm_source": "test"}
+    same = bench.kernel_roofline("neighbors", 0.05, ("hbm", 1e6), peaks)
+    assert same["traffic"] == 1000 and same["issue"]["warp_inst_per_launch"] == 5000.0
+    assert "traffic_source" not in same
+    big = bench.kernel_roofline("neighbors", 0.05, ("hbm", 1e6), peaks, 10 * bench.NCU_CAPTURE_N_FLUID)
+    assert big["traffic"] == 10000 and big["issue"]["warp_inst_per_launch"] == 50000.0
+    assert "scaled" in big["traffic_source"] and "scaled" in big["issue"]["source"]
