@@ -1185,12 +1185,20 @@ class Sim final : public SimBase {
         if (nw_ == 0) return SPH_OK;
         {
             // the periodic form only where an axis wraps: the others compile its code out
+            // WLP lanes per wall particle, WLP_LARGE for large wall sets
+            const bool large = nw_ >= WLP_LARGE_MIN;
+            const int lanes = large ? WLP_LARGE : WLP;
             auto launch = [&](auto kernel) {
-                kernel<<<grid_for((int64_t)nw_ * WLP), BLOCK, 0, stream>>>(
+                kernel<<<grid_for((int64_t)nw_ * lanes), BLOCK, 0, stream>>>(
                     C_, nw_, fstart_, wpos_, wcell_, pos_[0], vel_cur, wrho_, wtag_, d_tag_, d_geff_, d_active_, wnrm_);
             };
-            SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
-                       P_.periodic ? launch(k_wall_pressure<T, true>) : launch(k_wall_pressure<T, false>));
+            if (large)
+                SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
+                           P_.periodic ? launch(k_wall_pressure<T, true, WLP_LARGE>)
+                                       : launch(k_wall_pressure<T, false, WLP_LARGE>));
+            else
+                SPH_KERNEL(SPH_K_WALL_PRESSURE, 1,
+                           P_.periodic ? launch(k_wall_pressure<T, true>) : launch(k_wall_pressure<T, false>));
         }
         return SPH_OK;
     }

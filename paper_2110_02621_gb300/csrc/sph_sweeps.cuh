@@ -32,7 +32,9 @@ namespace sph {
 constexpr int LP = 4;        // lanes per target particle
 constexpr int SUBF = 40;     // fluid entries per lane sub-list (about 80/LP used)
 constexpr int SUBW = 16;     // wall entries per lane sub-list
-constexpr int WLP = 8;       // lanes per wall particle in the wall-pressure sweep
+constexpr int WLP = 8;       // lanes per wall particle in the wall-pressure sweep (WLP_LARGE from
+constexpr int WLP_LARGE = 4; // WLP_LARGE_MIN wall particles on: measured faster at 0.36 M and 2.2 M walls,
+constexpr int WLP_LARGE_MIN = 250000;  // slower at 0.12 M, where 4 lanes leave too few threads in flight
 constexpr int AWLP = 4;      // lanes per wall particle in the adjoint's wall sweeps
 constexpr int LBLOCK = 128;  // threads per block
 
@@ -75,7 +77,7 @@ __device__ __forceinline__ T minus_ref(T s, T c, T ref_hi, T ref_lo)
     return (s - ref_hi) - (c + ref_lo);
 }
 
-// The G lanes of a particle (G = LP, WLP or AWLP for wall particles)
+// The G lanes of a particle (G = LP, WLP, WLP_LARGE or AWLP for wall particles)
 // always take the same path (everything they branch on is per particle),
 // while different groups of a warp may not: the group shuffles therefore
 // name only the group's own lanes.
@@ -634,12 +636,12 @@ __device__ __forceinline__ T wall_density(const PhaseK<T>& P, const Cfg<T>& C, T
 //   p_w = sum_f (p_f + rho_f g.r_wf) w_wf / sum_f w_wf,  r_wf = r_w - r_f,
 // w = W (one phase) or W/rho_f (several phases, Sec. 2.3).  Walls without
 // fluid support (not tagged by this step's neighbour build) get p_w = 0 and
-// rho_w = rho0 at once; the others split the fluid of their 27 cells over WLP
+// rho_w = rho0 at once; the others split the fluid of their 27 cells over G
 // lanes.  rho_w = rho0 + EOS^-1(p_w) per phase, at least rho0/2.
 // The same scan marks the wall particles through which the penalty acts
 // (wnrm.w = 1, else 0): some fluid of the support lies on the side n_w
 // points to.
-template <class T, bool PER>
+template <class T, bool PER, int G = WLP>
 __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
     Cfg<T> C, int32_t nw, const int32_t* __restrict__ fstart, V4<T>* __restrict__ wpos,
     const int4* __restrict__ wcell, const V4<T>* __restrict__ pos, const V4<T>* __restrict__ vel,
@@ -647,7 +649,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
     const V4<T>* __restrict__ geff, unsigned long long* active, V4<T>* __restrict__ wnrm)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int w = t / WLP;
+    const int w = t / G;
     int has = 0;
     if (w < nw) {
         const bool multi = C.n_phases > 1;
@@ -658,7 +660,7 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
             const int4 c = wcell[w];
             const V4<T> pw = wpos[w];
             const V4<T> nn = wnrm[w];
-            scan_compact<PER, WLP>(C, c, pw, fstart, pos, t % WLP, [&](int j, T rx, T ry, T rz, T r2, int) {
+            scan_compact<PER, G>(C, c, pw, fstart, pos, t % G, [&](int j, T rx, T ry, T rz, T r2, int) {
                 const T W = kernel_W(C, r2 * p_rsqrt(r2));
                 const T p_f = reinterpret_cast<const T*>(pos + j)[3];
                 const T rho_f = vel[j].w;
@@ -667,11 +669,11 @@ __global__ void __launch_bounds__(LBLOCK) k_wall_pressure(
                 den += om;
                 front |= rx * nn.x + ry * nn.y + rz * nn.z < T(0);  // (r_f - r_w).n_w > 0
             });
-            num = group_sum<WLP>(num);
-            den = group_sum<WLP>(den);
-            front = (__ballot_sync(group_mask<WLP>(), front) & group_mask<WLP>()) != 0u;
+            num = group_sum<G>(num);
+            den = group_sum<G>(den);
+            front = (__ballot_sync(group_mask<G>(), front) & group_mask<G>()) != 0u;
         }
-        if (t % WLP == 0) {
+        if (t % G == 0) {
             const T p_w = den > T(0) ? num / den : T(0);
             has = den > T(0);
             reinterpret_cast<T*>(wpos + w)[3] = p_w;
