@@ -31,7 +31,10 @@ namespace sph {
 
 constexpr int LP = 4;        // lanes per target particle
 constexpr int SUBF = 40;     // fluid entries per lane sub-list (about 80/LP used)
-constexpr int SUBW = 16;     // wall entries per lane sub-list
+constexpr int SUBW = 24;     // wall entries per lane sub-list: a particle at a tank edge has up to
+                             // ~60 wall neighbours, and one lane past its capacity sends the particle's
+                             // sweeps to the cell scan (with 16, 4-6 particles of the 80 k dam break
+                             // did, and their warps set the sweeps' length: 190.7 against 174.4 us)
 constexpr int WLP = 8;       // lanes per wall particle in the wall-pressure sweep (WLP_LARGE from
 constexpr int WLP_LARGE = 4; // WLP_LARGE_MIN wall particles on: measured faster at 0.36 M and 2.2 M walls,
 constexpr int WLP_LARGE_MIN = 250000;  // slower at 0.12 M, where 4 lanes leave too few threads in flight
