@@ -503,6 +503,9 @@ def run_gpu(args):
     launches1 = sum(v["launches"] for v in prof.values())
     active_mean = (act_steps1 - act_steps0) / max(steps1 - steps0, 1)
     ff1, fw1 = sim.neighbor_totals()
+    # fluid particles whose fluid / wall list overflowed at the end of the
+    # timed steps (their sweeps scan the cells instead)
+    list_overflow = sim.neighbor_overflow()
     cand_tests = candidate_tests(sim)
     # the dominant kernel's launch duration, CUDA events around each launch,
     # on the steps that follow the timed region (same workload, cold L2)
@@ -549,6 +552,7 @@ def run_gpu(args):
             "roofline": roofline, "step_roofline": step_roof, "step_roofline_design": step_roof_design,
             "streaming_roofline": streaming,
             "pairs_per_fluid_particle": {"fluid": pairs_ff / sc.n_fluid, "wall": pairs_fw / sc.n_fluid},
+            "list_overflow_particles": {"fluid": list_overflow[0], "wall": list_overflow[1]},
             "gpu_launches": int(launches1 - launches0), "clocks": clk,
             "host_wall_s": wall1 - wall0}
 

@@ -483,6 +483,15 @@ class Simulation:
         _check(sph_get_neighbors(self.ctx, f_off, None, 0, w_off, None, 0, None), self.ctx)
         return int(f_off[-1]), int(w_off[-1])
 
+    def neighbor_overflow(self):
+        """(fluid, wall): the number of fluid particles whose fluid / wall list
+        of the last build overflowed (their sweeps scan the cells)."""
+        n = self.nf
+        f_off, w_off = np.zeros(n + 1, np.int64), np.zeros(n + 1, np.int64)
+        ovf = np.zeros(2, np.int64)
+        _check(sph_get_neighbors(self.ctx, f_off, None, 0, w_off, None, 0, ovf), self.ctx)
+        return int(ovf[0]), int(ovf[1])
+
     def diagnostics(self) -> np.ndarray:
         out = np.zeros(8)
         _check(sph_diagnostics(self.ctx, out), self.ctx)
